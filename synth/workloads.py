@@ -1,0 +1,250 @@
+"""Workload descriptions with seeded synthetic models (input generation only).
+
+Index conventions used everywhere in this repository:
+
+* A grid axis has ``n`` intervals and ``n + 1`` points; axis 0 is z (slowest), then y (3-D only), then x
+  (fastest, contiguous).
+* Each axis is cut into ``p`` patches of ``M = n / p`` intervals (the paper's Sec. 3.2); junction points
+  are stored once.
+* Velocity components: ``v1`` is along x, ``v2`` along y, ``v3`` along z (the paper's x_1, x_2, x_3).
+
+The five standard workloads follow the paper's experiments in shape (2-D acoustic and 3-D elastic
+velocity-stress propagation with a Ricker point source, Sec. 4) at the sizes of the benchmark table:
+a small 2-D parity case, a 2-D layered model with a Gaussian-correlated perturbation, a 3-D homogeneous
+elastic model, a 3-D smooth heterogeneous elastic model for the adjoint, and a batch of 2-D shots with
+uneven grid sizes.  Every random draw is seeded.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Dict, Optional, Tuple
+
+import numpy as np
+from scipy.ndimage import gaussian_filter
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dim: int
+    physics: str  # "acoustic" or "elastic"
+    n: Tuple[int, ...]  # intervals per axis, axis 0 = z
+    p: Tuple[int, ...]  # patches per axis
+    h: Tuple[float, ...]  # spacing per axis [m]
+    n_nb: int  # PMBC halo width
+    dt: float  # time step [s]
+    steps: int
+    model_fn: Callable[[], Tuple[np.ndarray, Optional[np.ndarray], np.ndarray]]
+    src_index: Tuple[int, ...]
+    src_kinds: Tuple[str, ...]  # subset of "pressure", "explosive", "shear_xz", "force_z"
+    f0: float  # Ricker peak frequency [Hz]
+    t0: float  # Ricker delay [s]
+    amp: float = 1.0
+    receivers: Dict[str, np.ndarray] = dataclasses.field(default_factory=dict)  # field -> flat indices
+    precision: str = "fp64"
+    checkpoint_every: int = 0
+    seed: int = 0
+
+    @property
+    def shape(self) -> Tuple[int, ...]:
+        return tuple(int(k) + 1 for k in self.n)
+
+    @property
+    def points(self) -> int:
+        return int(np.prod(self.shape))
+
+    def model(self):
+        """(vp, vs, rho) as float64 arrays of the grid shape; vs is None for acoustic workloads."""
+        return self.model_fn()
+
+
+def random_field(shape, seed: int, corr_cells: float) -> np.ndarray:
+    """White noise (seeded) smoothed by a Gaussian of std ``corr_cells`` cells, renormalised to zero mean
+    and unit standard deviation."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(shape)
+    if corr_cells > 0:
+        g = gaussian_filter(g, sigma=corr_cells, mode="reflect")
+    g = g - g.mean()
+    return g / g.std()
+
+
+def _cfl_dt(h: float, vmax: float, cfl: float = 0.4) -> float:
+    return cfl * h / vmax
+
+
+def _top_row_receivers(shape) -> np.ndarray:
+    """Flat indices of every point on the plane z = 0 (axis-0 index 0)."""
+    return np.arange(int(np.prod(shape[1:])), dtype=np.int64)
+
+
+def acoustic2d_small(n: int = 128, p: int = 2, steps: int = 300, n_nb: int = 12) -> Workload:
+    """2-D acoustic, constant v = 2000 m/s, rho = 1000 kg/m^3, h = 10 m, Ricker 15 Hz at the centre, FP64."""
+    shape = (n + 1, n + 1)
+    h = 10.0
+
+    def model():
+        return np.full(shape, 2000.0), None, np.full(shape, 1000.0)
+
+    f0 = 15.0
+    return Workload(
+        name=f"acoustic2d_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h), n_nb=n_nb,
+        dt=_cfl_dt(h, 2000.0), steps=steps, model_fn=model, src_index=(n // 2, n // 2),
+        src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
+        receivers={"sigma": _top_row_receivers(shape)}, precision="fp64")
+
+
+def _layered_velocity_2d(n: int, seed: int) -> np.ndarray:
+    """Three layers (1500 / 2500 / 3500 m/s by depth thirds) times (1 + 0.05 g), g Gaussian-correlated with
+    a 50 m correlation length (5 cells at h = 10 m)."""
+    shape = (n + 1, n + 1)
+    z = np.arange(n + 1)[:, None] * np.ones((1, n + 1))
+    v = np.where(z < n / 3, 1500.0, np.where(z < 2 * n / 3, 2500.0, 3500.0))
+    g = random_field(shape, seed, corr_cells=5.0)
+    return v * (1.0 + 0.05 * g)
+
+
+def acoustic2d_layered(n: int = 2048, p: int = 8, steps: int = 2000, n_nb: int = 20,
+                       precision: str = "fp32_kahan", seed: int = 2002) -> Workload:
+    """2-D acoustic three-layer model with a 5 % Gaussian-correlated perturbation, Ricker 20 Hz at the centre."""
+    shape = (n + 1, n + 1)
+    h = 10.0
+    vp = _layered_velocity_2d(n, seed)
+    vmax = float(vp.max())
+
+    def model():
+        return vp.copy(), None, np.full(shape, 1000.0)
+
+    f0 = 20.0
+    return Workload(
+        name=f"acoustic2d_layered_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h),
+        n_nb=n_nb, dt=_cfl_dt(h, vmax), steps=steps, model_fn=model, src_index=(n // 2, n // 2),
+        src_kinds=("pressure",), f0=f0, t0=1.2 / f0, receivers={"sigma": _top_row_receivers(shape)},
+        precision=precision, seed=seed)
+
+
+def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int = 20,
+                          precision: str = "fp32_kahan") -> Workload:
+    """3-D isotropic elastic, vp = 3000, vs = 1730, rho = 2000, explosive plus shear source at the centre,
+    15 Hz Ricker, receivers v1, v2, v3 on the top plane."""
+    shape = (n + 1,) * 3
+    h = 10.0
+
+    def model():
+        return np.full(shape, 3000.0), np.full(shape, 1730.0), np.full(shape, 2000.0)
+
+    f0 = 15.0
+    top = _top_row_receivers(shape)
+    return Workload(
+        name=f"elastic3d_homog_{n}_p{p}", dim=3, physics="elastic", n=(n,) * 3, p=(p,) * 3, h=(h,) * 3,
+        n_nb=n_nb, dt=_cfl_dt(h, 3000.0), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
+        src_kinds=("explosive", "shear_xz"), f0=f0, t0=1.2 / f0,
+        receivers={"v1": top, "v2": top, "v3": top}, precision=precision)
+
+
+def elastic3d_heterogeneous(n: int = 192, p: int = 4, steps: int = 1500, n_nb: int = 20,
+                            precision: str = "fp32_kahan", seeds=(4001, 4002, 4003),
+                            true_model: bool = True) -> Workload:
+    """3-D elastic with smooth random vp/vs/rho (5 %, 100 m correlation length, clipped so vp/vs >= 1.5).
+    ``true_model=False`` gives the homogeneous starting model of the inversion."""
+    shape = (n + 1,) * 3
+    h = 10.0
+    corr = 100.0 / h
+
+    def model():
+        if not true_model:
+            return np.full(shape, 3000.0), np.full(shape, 1730.0), np.full(shape, 2000.0)
+        vp = 3000.0 * (1.0 + 0.05 * random_field(shape, seeds[0], corr))
+        vs = 1730.0 * (1.0 + 0.05 * random_field(shape, seeds[1], corr))
+        rho = 2000.0 * (1.0 + 0.05 * random_field(shape, seeds[2], corr))
+        vs = np.minimum(vs, vp / 1.5)
+        return vp, vs, rho
+
+    vmax = 3000.0 * 1.25  # 5-sigma bound of the perturbed vp; keeps one dt for the true and start models
+    f0 = 15.0
+    return Workload(
+        name=f"elastic3d_hetero_{n}_p{p}", dim=3, physics="elastic", n=(n,) * 3, p=(p,) * 3, h=(h,) * 3,
+        n_nb=n_nb, dt=_cfl_dt(h, vmax), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
+        src_kinds=("explosive", "shear_xz"), f0=f0, t0=1.2 / f0,
+        receivers={"v3": _top_row_receivers(shape)}, precision=precision,
+        checkpoint_every=int(math.ceil(math.sqrt(steps))), seed=seeds[0])
+
+
+def batched_shots(n_shots: int = 64, steps: int = 1500, n_nb: int = 20, seed: int = 5000,
+                  sizes=tuple(range(512, 2049, 128)), M: int = 128, precision: str = "fp32"):
+    """Shots of a 2-D acoustic survey with uneven square grids: n_s drawn uniformly from ``sizes`` (multiples
+    of M), p_s = n_s / M patches per axis, 3-5 horizontal layers with v ~ U[1500, 4000] sorted by depth,
+    rho = 1000, Ricker 20 Hz at (z = 5, x = n_s / 2)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=n_shots)
+    out = []
+    h = 10.0
+    for s, n in enumerate(ns):
+        n = int(n)
+        r = np.random.default_rng(seed + 1 + s)
+        n_layers = int(r.integers(3, 6))
+        v_layers = np.sort(r.uniform(1500.0, 4000.0, size=n_layers))
+        bounds = np.sort(r.uniform(0.1, 0.9, size=n_layers - 1)) * n
+        shape = (n + 1, n + 1)
+
+        def model(n=n, v_layers=v_layers, bounds=bounds, shape=shape):
+            z = np.arange(n + 1, dtype=np.float64)
+            vz = v_layers[np.searchsorted(bounds, z, side="right")]
+            return np.repeat(vz[:, None], n + 1, axis=1), None, np.full(shape, 1000.0)
+
+        f0 = 20.0
+        out.append(Workload(
+            name=f"shot{s}_{n}", dim=2, physics="acoustic", n=(n, n), p=(n // M, n // M), h=(h, h),
+            n_nb=n_nb, dt=_cfl_dt(h, float(v_layers.max())), steps=steps, model_fn=model,
+            src_index=(5, n // 2), src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
+            receivers={"sigma": _top_row_receivers(shape)}, precision=precision, seed=seed + 1 + s))
+    return out
+
+
+def gaussian_pulse_2d(n: int, p: int, n_nb: int = 20, dt: float = 1e-4, steps: int = 200):
+    """The paper's 2-D convergence setup (Sec. 4.1): [-5, 5]^2, c = 50 m/s, rho = 1, zero velocity and the
+    initial pressure exp(-5 (x^2 + z^2)); no source.  Returns (workload, initial sigma)."""
+    shape = (n + 1, n + 1)
+    h = 10.0 / n
+    x = -5.0 + h * np.arange(n + 1)
+    sigma0 = np.exp(-5.0 * (x[:, None] ** 2 + x[None, :] ** 2))
+
+    def model():
+        return np.full(shape, 50.0), None, np.full(shape, 1.0)
+
+    w = Workload(name=f"gauss2d_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h),
+                 n_nb=n_nb, dt=dt, steps=steps, model_fn=model, src_index=(n // 2, n // 2), src_kinds=(),
+                 f0=1.0, t0=0.0, amp=0.0, precision="fp64")
+    return w, sigma0
+
+
+def scaled(w: Workload, n: int, p: int, steps: int, n_nb: Optional[int] = None) -> Workload:
+    """A smaller copy of an acoustic/elastic workload on an n-interval grid (same physics, h, dt, source
+    type), used for parity cases that the oracle finishes in seconds.  Models are rebuilt at the new size
+    with the same recipe (constant or freshly seeded)."""
+    d = w.dim
+    shape = (n + 1,) * d
+    vp0, vs0, rho0 = w.model()
+    # Resample the model by nearest-point lookup so that layered structure is kept.
+    idx = [np.minimum((np.arange(n + 1) * (w.n[a] / n)).round().astype(int), w.n[a]) for a in range(d)]
+    sl = np.ix_(*idx)
+    vp = vp0[sl]
+    vs = None if vs0 is None else vs0[sl]
+    rho = rho0[sl]
+
+    def model():
+        return vp.copy(), (None if vs is None else vs.copy()), rho.copy()
+
+    rec = {k: np.arange(int(np.prod(shape[1:])), dtype=np.int64) for k in w.receivers}
+    return dataclasses.replace(
+        w, name=f"{w.name}_as{n}_p{p}", n=(n,) * d, p=(p,) * d, steps=steps, model_fn=model,
+        n_nb=w.n_nb if n_nb is None else n_nb, src_index=tuple(n // 2 for _ in range(d)), receivers=rec)
+
+
+WORKLOADS = {
+    "acoustic2d_small": acoustic2d_small,
+    "acoustic2d_layered": acoustic2d_layered,
+    "elastic3d_homogeneous": elastic3d_homogeneous,
+    "elastic3d_heterogeneous": elastic3d_heterogeneous,
+}
