@@ -1,0 +1,335 @@
+"""Benchmark of the LOSS time step on one GB300 (or N replicas, one per GPU).
+
+Workload: the 2-D acoustic layered model on 2049 x 2049 points in 8 x 8 patches (M = 256), PMBC halo width 20,
+h = 10 m, 3-layer velocity (1500/2500/3500 m/s) times a 5 % Gaussian-correlated perturbation (seed 2002),
+Ricker 20 Hz at the centre, CFL 0.4, a 40-point ADE-PML layer on every side.  One step = one Strang step of
+the whole hot path (PMBC closures, local spline solves, derivatives, velocity-stress update, PML memory
+variables, source, receivers on the top row).  Headline precision: FP32 fields with Kahan-compensated updates
+(PMBC sums in FP64); the FP64 form is measured alongside.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the library's stream, with an L2
+flush (write + read of a buffer larger than L2) between timed steps; barrier + synchronize around the timed
+region; the max over ranks is reported.  value = whole-job grid-point updates per second (sum over ranks).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt updates/s per step on 1 GB300 (FP32 vs FP64) at stated L2 err; HBM GB/s frac"
+UNIT = "pt-upd/s"
+WORKLOAD = "acoustic2d_layered 2049x2049 pts, 8x8 patches (M=256), n_nb=20, PML 40, 3-layer + 5% noise, Ricker 20 Hz"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _flusher(torch, dev):
+    """Write then read a 512 MiB buffer (L2 is ~129 MiB): evicts our data and leaves clean lines."""
+    a = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    b = torch.ones(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def flush():
+        a.fill_(1.0)
+        b.sum()
+
+    return flush
+
+
+def _timed_steps(torch, g, steps, flush):
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(1)
+        e1.record(st)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def _alg_bytes_per_point(kernel, esize, kahan, pml_frac):
+    """Algorithmic DRAM bytes per grid point of one launch (each array the kernel must touch, once)."""
+    if kernel == "acoustic_x":
+        # read v1, sigma, kappa, b, d_z v3; write sigma, v1 (+ compensation of sigma and v1 read and written)
+        n = 5 + 2 + (4 if kahan else 0)
+    else:
+        # read sigma, v3, b; write v3, d_z v3 (+ compensation of v3 read and written)
+        n = 3 + 2 + (2 if kahan else 0)
+    return n * esize
+
+
+def run_ours(args):
+    import torch
+    import paper_2301_05127_gb300 as pkg
+    from synth import acoustic2d_layered
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = _flusher(torch, dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = acoustic2d_layered(precision="fp32_kahan")
+    pts = w.points
+
+    # --- headline: FP32 + Kahan -------------------------------------------------------------------------
+    g = pkg.Grid.from_workloads([w])
+    g.step(args.warmup)
+    g.sync()
+    g.profile(True)
+    clk = Clocks(local)
+    barrier()
+    clk.start()
+    t_wall = time.perf_counter()
+    step_ms = _timed_steps(torch, g, args.steps, flush)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    launches = g.profile_read(-1)[1]
+    kern = {k: g.profile_read(k) for k in ("acoustic_x", "acoustic_z", "gather")}
+    g.profile(False)
+    sum_ms = max_over_ranks(sum(step_ms))
+    ms_per_step = sum_ms / args.steps
+    value = ws * pts / (ms_per_step * 1e-3)
+
+    # dominant kernel roofline
+    dom = max(("acoustic_x", "acoustic_z"), key=lambda k: kern[k][0])
+    dom_ms = kern[dom][0] / max(kern[dom][1], 1)
+    pml_frac = 0.0
+    alg = _alg_bytes_per_point(dom, 4, True, pml_frac) * pts
+    peak, peak_kind = _peaks()
+    achieved = alg / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(dom)
+        except Exception:
+            traffic = None
+
+    # accuracy of the timed FP32 run against the FP64 form of the same run (the FP64 form matches the FP64
+    # oracle in the parity tests)
+    s32 = g.get_field(0, "sigma").astype(np.float64)
+
+    # --- FP64 form ---------------------------------------------------------------------------------------
+    g64 = pkg.Grid.from_workloads([w], precision="fp64")
+    g64.step(args.warmup)
+    g64.sync()
+    n64 = max(1, min(args.steps, max(3, args.steps // 2)))
+    ms64 = _timed_steps(torch, g64, n64, flush)
+    fp64_ms = max_over_ranks(sum(ms64)) / len(ms64)
+    # same number of steps as the FP32 run for the accuracy comparison
+    if args.steps > len(ms64):
+        g64.step(args.steps - len(ms64))
+    s64 = g64.get_field(0, "sigma")
+    rel_fp32 = float(np.linalg.norm(s32 - s64) / max(np.linalg.norm(s64), 1e-300))
+    g64.close()
+    g.close()
+
+    # --- end to end through the public API with host buffers ---------------------------------------------
+    ge = pkg.Grid.from_workloads([w])
+    shape = w.shape
+    host_in = [torch.zeros(shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+    host_in[0].copy_(torch.from_numpy(np.zeros(shape, np.float32)))
+    host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+    ge.step(1)  # graph of kernels warm (stagger prologue paid in the timed region below anyway)
+    ge.sync()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f, hb in zip(("sigma", "v1", "v3"), host_in):
+        ge.set_field(0, f, hb)
+    ge.step(args.steps)
+    tr = ge.record(0)["_all"]
+    ge.get_field(0, "sigma", out=host_out)
+    e1.record()
+    e1.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    h2d = 3 * pts * 4
+    d2h = pts * 4 + tr.nbytes
+    ge.close()
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": pts, "precision": "fp32 + Kahan compensation, PMBC sums fp64",
+                       "l2": "flushed between timed steps (512 MiB write + read)", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "alg_bytes_per_launch": alg, "avg_launch_ms": dom_ms},
+            "kernels_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in kern.items()},
+            "fp64": {"value": ws * pts / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "unit": UNIT},
+            "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + args.steps},
+            "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "wall_s_timed_region": t_wall,
+        }
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return out
+
+
+def _oracle_steps(steps, warmup):
+    """Time the FP64 oracle on the benchmark workload: each step a full Strang step of the full grid."""
+    from oracle.wave import Simulation
+    from synth import acoustic2d_layered
+
+    w = acoustic2d_layered(precision="fp64")
+    sim = Simulation(w)
+    sim.step(warmup, record=False)
+    c0, t0 = time.process_time(), time.perf_counter()
+    sim.step(steps, record=False)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    return w.points * steps / wall, max(1, round(cpu / wall)), wall
+
+
+def cpu_baseline():
+    v, cores, wall = _oracle_steps(steps=2, warmup=0)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 full Strang steps of the 2049^2 FP64 oracle ({wall:.1f} s); host {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    v, cores, wall = _oracle_steps(args.steps, args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": 2049 * 2049, "precision": "fp64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v,
+                             "sample": f"{args.steps} full Strang steps of the 2049^2 FP64 oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_ours(args)
+        if out is not None:
+            ws = _dist()[0]
+            out["cpu_baseline"] = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

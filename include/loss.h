@@ -1,0 +1,205 @@
+/*
+ * loss.h -- C ABI of the GB300 (sm_103a) implementation of the distributed local spline simulator
+ * (LOSS) time step: Guo, Li, Xiong, "Distributed local spline simulator for wave propagation",
+ * arXiv 2301.05127.
+ *
+ * What one step computes (paper Sec. 2 and 3):
+ *   - along every grid line of every axis, cubic-B-spline collocation (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
+ *     solved patch by patch (Eq. spline_cofficient_eq_piece), each patch closed by the perfectly matched
+ *     boundary condition (PMBC, Eqs. PMBC / PMBC_coeffcients and the end closures of Sec. 3.2):
+ *     truncated sums over n_nb samples on each side of every junction;
+ *   - first derivatives (c_{i+1} - c_{i-1})/(2h) (Eq. derivative_approximation);
+ *   - the acoustic (Eq. acoustic_wave) or elastic velocity-stress update (Sec. 2) advanced by the Strang
+ *     splitting "half A, full B, half A" of Sec. 3.3 (A: velocities, B: stresses).
+ *
+ * Conventions shared by every entry point:
+ *   - A grid axis has n intervals and n + 1 points.  Axis 0 is z (slowest), axis 1 is y (3-D only),
+ *     the last axis is x (contiguous).  In 2-D the axes are (z, x) and n[2], p[2], h[2] are ignored.
+ *   - Each axis is cut into p patches of M = n / p intervals; junction points are stored once.
+ *   - Host-visible arrays are dense, row-major [z][y][x] (2-D: [z][x]); "flat index" means the offset in
+ *     that dense array.
+ *   - Field arrays are in the working precision of the grid (double for LOSS_FP64, float otherwise).
+ *     Model arrays (vp, vs, rho) are always double.
+ *   - mem = LOSS_MEM_HOST for host pointers, LOSS_MEM_DEVICE for device pointers of the current CUDA
+ *     device.  Caller buffers are only read or written during the call, or, for device pointers, by work
+ *     queued on the handle's stream before the call returns; loss_sync() waits for that work.
+ *   - The library owns every device allocation it makes (through the caller's allocator if one is given)
+ *     and frees them in loss_destroy().
+ *   - Every entry point returns a status and never aborts.  After LOSS_E_CUDA or LOSS_E_TIMEOUT the handle
+ *     is poisoned: every later call except loss_destroy / loss_last_error returns the same status.
+ *     loss_last_error() describes the most recent failure on a handle.
+ */
+#ifndef LOSS_H_
+#define LOSS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct loss_ctx* loss_handle_t; /* opaque; owned by the library */
+
+typedef enum {
+  LOSS_OK = 0,
+  LOSS_E_ARG = 1,         /* bad argument (null pointer, out-of-range index, unknown enum) */
+  LOSS_E_SHAPE = 2,       /* grid shape violates a rule listed at loss_create_grid */
+  LOSS_E_NOMEM = 3,       /* device or host allocation failed */
+  LOSS_E_CUDA = 4,        /* a CUDA call failed; handle poisoned */
+  LOSS_E_STATE = 5,       /* call not valid in the handle's current state */
+  LOSS_E_TIMEOUT = 6,     /* a bounded device wait expired; handle poisoned */
+  LOSS_E_NUMERIC = 7,     /* non-finite values detected */
+  LOSS_E_UNSUPPORTED = 8  /* valid request this build cannot serve (e.g. a line longer than fits on chip) */
+} loss_status_t;
+
+enum { LOSS_ACOUSTIC = 0, LOSS_ELASTIC = 1 };
+enum { LOSS_FP64 = 0, LOSS_FP32 = 1, LOSS_FP32_KAHAN = 2 };
+enum { LOSS_MEM_HOST = 0, LOSS_MEM_DEVICE = 1 };
+
+/* Field identifiers.  Acoustic grids use V1, V3 (2-D) or V1, V2, V3 (3-D) and SIGMA (the pressure, which
+ * shares the slot of S11).  Elastic grids use all nine. */
+enum {
+  LOSS_FIELD_V1 = 0, LOSS_FIELD_V2 = 1, LOSS_FIELD_V3 = 2,
+  LOSS_FIELD_S11 = 3, LOSS_FIELD_S22 = 4, LOSS_FIELD_S33 = 5,
+  LOSS_FIELD_S12 = 6, LOSS_FIELD_S13 = 7, LOSS_FIELD_S23 = 8,
+  LOSS_FIELD_SIGMA = 3,
+  LOSS_NUM_FIELDS = 9
+};
+
+/* Source kinds (bit mask).  PRESSURE acts on the acoustic pressure, EXPLOSIVE on S11, S22, S33, SHEAR_XZ
+ * on S13 (all in the stress sub-step B, evaluated at t_n + dt/2); FORCE_Z is a body force on V3 in each
+ * half of the velocity sub-step A (at t_n and t_{n+1}). */
+enum { LOSS_SRC_PRESSURE = 1u, LOSS_SRC_EXPLOSIVE = 2u, LOSS_SRC_SHEAR_XZ = 4u, LOSS_SRC_FORCE_Z = 8u };
+
+typedef struct {
+  int32_t dim;       /* 2 or 3 */
+  int32_t physics;   /* LOSS_ACOUSTIC or LOSS_ELASTIC (elastic requires dim == 3) */
+  int32_t precision; /* LOSS_FP64, LOSS_FP32 or LOSS_FP32_KAHAN */
+  int32_t n_nb;      /* PMBC halo width (paper Sec. 3.2): terms m = -n_nb..n_nb around each junction */
+  int64_t n[3];      /* intervals per axis (axis 0 = z) */
+  int32_t p[3];      /* patches per axis */
+  double h[3];       /* grid spacing per axis [m] */
+  double dt;         /* time step [s] */
+} loss_grid_desc_t;
+
+/* Optional device allocator.  alloc(ctx, bytes, stream) returns device memory (or NULL on failure);
+ * free(ctx, ptr, stream) releases it.  stream is the handle's cudaStream_t. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, void* stream);
+} loss_allocator_t;
+
+/* Version string of the library. */
+const char* loss_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* loss_status_str(loss_status_t status);
+
+/* Text of the last failure on this handle (empty if none); valid until the next call on the handle. */
+const char* loss_last_error(loss_handle_t handle);
+
+/* Create a handle holding n_shots independent grids (shots), all resident on the current CUDA device and
+ * advanced together by loss_step.  descs[s] describes shot s (paper Sec. 3.2 for the patch layout).
+ * Shape rules (else LOSS_E_SHAPE): dim in {2, 3}; every used n[a] >= 2 and n[a] % p[a] == 0;
+ * M = n/p >= 2 and n_nb <= M on every axis; n_nb >= 1; h > 0; dt > 0; elastic only with dim == 3.
+ * Lines longer than fit in one thread block's shared memory give LOSS_E_UNSUPPORTED.
+ * alloc may be NULL (then cudaMallocAsync / cudaFreeAsync on the stream are used).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out is a new handle; on failure *out = NULL.
+ * Fields, compensation terms and the model start at zero; the source is off; no receivers. */
+loss_status_t loss_create_grid(const loss_grid_desc_t* descs, int32_t n_shots, const loss_allocator_t* alloc,
+                               void* cuda_stream, loss_handle_t* out);
+
+/* Release every resource of the handle (waits for its stream first).  NULL is accepted. */
+loss_status_t loss_destroy(loss_handle_t handle);
+
+/* Set the model of one shot from dense double arrays of the grid shape: P velocity vp, S velocity vs
+ * (elastic only; pass NULL for acoustic grids) and density rho.  Stored as kappa = rho vp^2 and b = 1/rho
+ * (acoustic) or lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2, b = 1/rho (elastic), paper Sec. 2.
+ * Arrays are copied.  LOSS_E_ARG if rho <= 0 anywhere or a required pointer is NULL. */
+loss_status_t loss_set_model(loss_handle_t handle, int32_t shot, const double* vp, const double* vs,
+                             const double* rho, int32_t mem);
+
+/* Ricker source f_r(t) = (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (paper Sec. 4.2), with the Gaussian
+ * spatial amplitude of Sec. 4.2: exp(-|o|^2 / 8) over integer offsets o (standard deviation 2 cells per
+ * axis), truncated to |o_a| <= 12 and to the grid, scaled so that its sum times the cell volume equals amp.
+ * idx = centre point (z, y, x); for 2-D idx[1] is ignored.  kind_mask = 0 switches the source off. */
+loss_status_t loss_set_source(loss_handle_t handle, int32_t shot, const int64_t idx[3], uint32_t kind_mask,
+                              double amp, double f0, double t0);
+
+/* Absorbing layer: the ADE-PML of paper Sec. 3.3 in the outer `width` points of every axis (width = 0 turns it
+ * off), with profiles d = d0 r^2, k = 1 + (k_max - 1) r, alpha = pi f0 (1 - r) at normalised depth r, and
+ * d0 = -3 c_max log(R) / (2 width h), c_max = max vp of the model (so loss_set_model must come first, else
+ * LOSS_E_STATE).  Memory variables start at zero.  Each sub-step integrates the memory variables exactly
+ * with the other subsystem frozen (the exponential operator splitting of Sec. 3.3).
+ * LOSS_E_ARG unless 2 * width <= n on every axis, 0 < R < 1, k_max >= 1 and f0 > 0. */
+loss_status_t loss_set_pml(loss_handle_t handle, int32_t shot, int32_t width, double R, double k_max, double f0);
+
+/* Record field `field` of shot `shot` at the n dense flat indices flat_idx (int64, copied) after every
+ * step.  Replaces any earlier receiver set of that field; n = 0 removes it.  Recorded values are the
+ * fields at integer time levels t_{k} (k = steps taken so far). */
+loss_status_t loss_set_receivers(loss_handle_t handle, int32_t shot, int32_t field, const int64_t* flat_idx,
+                                 int64_t n, int32_t mem);
+
+/* Copy a dense field (working precision) into the state of one shot; resets that field's compensation. */
+loss_status_t loss_set_field(loss_handle_t handle, int32_t shot, int32_t field, const void* src, int32_t mem);
+
+/* Copy one field of one shot at the current integer time level into a dense array (working precision). */
+loss_status_t loss_get_field(loss_handle_t handle, int32_t shot, int32_t field, void* dst, int32_t mem);
+
+/* Advance every shot by n_steps Strang steps (paper Sec. 3.3), recording receivers after each step.
+ * Asynchronous on the handle's stream. */
+loss_status_t loss_step(loss_handle_t handle, int64_t n_steps);
+
+/* Number of recorded time levels and receivers of one shot (receivers of all fields, in increasing field
+ * id, each field in the order given to loss_set_receivers). */
+loss_status_t loss_record_count(loss_handle_t handle, int32_t shot, int64_t* n_steps, int64_t* n_receivers);
+
+/* Copy the traces of one shot, [n_steps][n_receivers] in working precision, and clear them. */
+loss_status_t loss_record(loss_handle_t handle, int32_t shot, void* out, int32_t mem);
+
+/* First (d1) and, if d2 != NULL, second (d2) LOSS derivative along `axis` of the dense field f given in the
+ * grid shape of `shot` (working precision; d1, d2 dense of the same shape).  d1 follows Eq.
+ * derivative_approximation with the PMBC closure; d2 = (c_{i-1} - 2 c_i + c_{i+1})/h^2 from the same local
+ * coefficients, averaged over the two patches at a shared junction.  axis: 0 = z, 1 = y (3-D), last = x. */
+loss_status_t loss_derivative(loss_handle_t handle, int32_t shot, int32_t axis, const void* f, void* d1, void* d2,
+                              int32_t mem);
+
+/* PMBC closure values phi (paper Eqs. PMBC and end closures) of the dense field f along `axis`: out has
+ * shape [lines][p + 1] in double, lines ordered as the dense array with `axis` removed. */
+loss_status_t loss_pmbc_phi(loss_handle_t handle, int32_t shot, int32_t axis, const void* f, double* phi, int32_t mem);
+
+/* Serialise / restore the full time-stepping state of every shot (fields, compensation terms, step
+ * counters) at the current integer time level.  loss_get_state with blob = NULL returns the size. */
+loss_status_t loss_get_state(loss_handle_t handle, void* blob, size_t* bytes);
+loss_status_t loss_set_state(loss_handle_t handle, const void* blob, size_t bytes);
+
+/* Number of steps taken by shot `shot`. */
+loss_status_t loss_get_step(loss_handle_t handle, int32_t shot, int64_t* step);
+
+/* Kernel identifiers for loss_profile_read. */
+enum {
+  LOSS_KERNEL_ACOUSTIC_X = 0, /* 2-D acoustic: stress sub-step and x part of the velocity sub-step on x lines */
+  LOSS_KERNEL_ACOUSTIC_Z = 1, /* 2-D acoustic: z part of the velocity sub-step and d_z v3 on z lines */
+  LOSS_KERNEL_GATHER = 2,     /* receiver gather */
+  LOSS_KERNEL_DERIVATIVE = 3, /* stand-alone derivative / phi (loss_derivative, loss_pmbc_phi) */
+  LOSS_NUM_KERNELS = 16
+};
+
+/* Reset the per-kernel counters of the handle and switch CUDA-event timing of every kernel launch on
+ * (enable != 0) or off.  Launches are always counted. */
+loss_status_t loss_profile(loss_handle_t handle, int32_t enable);
+
+/* Launches of kernel `kernel` since the last loss_profile call and, if timing was on, their summed device
+ * duration in milliseconds (waits for the stream).  kernel = -1 gives the totals over all kernels. */
+loss_status_t loss_profile_read(loss_handle_t handle, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* Wait for all work queued on the handle's stream. */
+loss_status_t loss_sync(loss_handle_t handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOSS_H_ */

@@ -18,6 +18,11 @@ exp(-(pi f0 (t - t0))^2), with the Gaussian spatial amplitude of Sec. 4.2 (class
 ("pressure", "explosive", "shear_xz") act in B and are evaluated at t_n + dt/2; a body force ("force_z")
 acts in each half of A, at t_n and at t_{n+1}.
 
+Absorbing layer (Sec. 3.3): an ADE-PML in the outer points of every axis with the exponential Strang
+splitting of the paper (class PML).  Without it the natural-spline ends impose no physical boundary condition
+and zero-frequency polynomial modes (uniform pressure fed by linear velocity fields) grow like a power of t
+from any rounding perturbation.
+
 Axes: array axis 0 is z, then y (3-D), then x.  v1 is along x, v2 along y, v3 along z.
 """
 from __future__ import annotations
@@ -112,6 +117,56 @@ class Source:
         field[self.block] += scale * ricker(t, self.f0, self.t0) * self.profile
 
 
+class PML:
+    """ADE-PML of Sec. 3.3 in the outer ``width`` points of every axis.
+
+    Profiles (Sec. 3.3 with m = p = 1): at normalised depth r in (0, 1] into a layer,
+        d = d0 r^2,  k = 1 + (k_max - 1) r,  alpha = alpha_max (1 - r),
+        d0 = -3 c_max log(R) / (2 L),  alpha_max = pi f0,  L = width * h.
+    Memory variables Psi_a (one per velocity derivative axis) and Phi_a (one per stress derivative axis) obey
+    dPsi/dt = -(d/k + alpha) Psi - (d/k^2) d_a(field) (Eq. ADE_PML_1).  With the other subsystem frozen each
+    sub-flow is integrated exactly (Eq. Euler_approximation and the exponential splitting that follows):
+        Psi(t + tau) = E Psi(t) - (d/k^2) (1 - E) / beta * g,         E = exp(-beta tau), beta = d/k + alpha,
+        field += sign * (coefficient) * [ (1/beta) (Psi(t+tau) - Psi(t)) - tau alpha / (d + alpha k) g ],
+    which reduces to field += sign * (coefficient) * (-tau g) outside the layers (d = 0, k = 1)."""
+
+    def __init__(self, n, h, width, R, k_max, f0, c_max):
+        self.width = int(width)
+        self.prof = []
+        for a in range(len(n)):
+            i = np.arange(n[a] + 1, dtype=np.float64)
+            if self.width > 0:
+                r = np.maximum(np.maximum(self.width - i, i - (n[a] - self.width)), 0.0) / self.width
+                L = self.width * h[a]
+                d0 = -3.0 * c_max * math.log(R) / (2.0 * L)
+            else:
+                r = np.zeros(n[a] + 1)
+                d0 = 0.0
+            d = d0 * r**2
+            k = 1.0 + (k_max - 1.0) * r
+            alpha = math.pi * f0 * (1.0 - r)
+            self.prof.append((d, k, alpha))
+
+    def _bc(self, a, dim):
+        shape = [1] * dim
+        shape[a] = -1
+        d, k, alpha = self.prof[a]
+        return d.reshape(shape), k.reshape(shape), alpha.reshape(shape)
+
+    def advance(self, mem: np.ndarray, g: np.ndarray, a: int, tau: float):
+        """Advance memory variable ``mem`` along axis ``a`` over ``tau`` with frozen derivative ``g``; return the
+        effective increment factor X such that field += sign * coefficient * X."""
+        d, k, alpha = self._bc(a, g.ndim)
+        in_layer = np.broadcast_to(d > 0, g.shape)
+        beta = d / k + alpha
+        with np.errstate(divide="ignore", invalid="ignore"):
+            E = np.exp(-beta * tau)
+            new = np.where(in_layer, E * mem - (d / k**2) * (1.0 - E) / beta * g, 0.0)
+            X = np.where(in_layer, (new - mem) / beta - tau * alpha / (d + alpha * k) * g, -tau * g)
+        mem[...] = new
+        return X
+
+
 def zero_state(physics: str, shape) -> Dict[str, np.ndarray]:
     names = ELASTIC_FIELDS if physics == "elastic" else (ACOUSTIC_FIELDS_2D if len(shape) == 2 else ACOUSTIC_FIELDS_3D)
     return {k: np.zeros(shape) for k in names}
@@ -121,24 +176,38 @@ def _velocity_names(dim):
     return (("v1", 1), ("v3", 3)) if dim == 2 else (("v1", 1), ("v2", 2), ("v3", 3))
 
 
-def acoustic_half_A(st, op, b, tau):
-    """Subsystem A for a time ``tau``: v_k <- v_k - tau * b * d_k sigma."""
+def acoustic_half_A(st, op, b, tau, pml: Optional[PML] = None, mem=None):
+    """Subsystem A for a time ``tau``: v_k <- v_k - tau * b * d_k sigma (Eq. acoustic_wave); with a PML the
+    exact exponential flow of Eq. ADE_PML_A."""
     for name, comp in _velocity_names(op.dim):
-        st[name] = st[name] - tau * b * op.Dc(st["sigma"], comp)
+        g = op.Dc(st["sigma"], comp)
+        if pml is None:
+            st[name] = st[name] - tau * b * g
+        else:
+            a = component_axis(comp, op.dim)
+            st[name] = st[name] + b * pml.advance(mem[f"psi{comp}"], g, a, tau)
 
 
-def acoustic_B(st, op, kappa, dt, src: Optional[Source], t_half):
-    """Subsystem B for a time ``dt``: sigma <- sigma - dt * kappa * div v, plus the pressure source."""
-    div = sum(op.Dc(st[name], comp) for name, comp in _velocity_names(op.dim))
-    st["sigma"] = st["sigma"] - dt * kappa * div
+def acoustic_B(st, op, kappa, dt, src: Optional[Source], t_half, pml: Optional[PML] = None, mem=None):
+    """Subsystem B for a time ``dt``: sigma <- sigma - dt * kappa * div v, plus the pressure source; with a PML
+    the exact exponential flow of Eq. ADE_PML_B."""
+    if pml is None:
+        div = sum(op.Dc(st[name], comp) for name, comp in _velocity_names(op.dim))
+        st["sigma"] = st["sigma"] - dt * kappa * div
+    else:
+        inc = 0.0
+        for name, comp in _velocity_names(op.dim):
+            a = component_axis(comp, op.dim)
+            inc = inc + pml.advance(mem[f"phi{comp}"], op.Dc(st[name], comp), a, dt)
+        st["sigma"] = st["sigma"] + kappa * inc
     if src is not None and "pressure" in src.kinds:
         src.add(st["sigma"], dt, t_half)
 
 
-def acoustic_step(st, op, kappa, b, dt, t_n, src=None):
-    acoustic_half_A(st, op, b, 0.5 * dt)
-    acoustic_B(st, op, kappa, dt, src, t_n + 0.5 * dt)
-    acoustic_half_A(st, op, b, 0.5 * dt)
+def acoustic_step(st, op, kappa, b, dt, t_n, src=None, pml=None, mem=None):
+    acoustic_half_A(st, op, b, 0.5 * dt, pml, mem)
+    acoustic_B(st, op, kappa, dt, src, t_n + 0.5 * dt, pml, mem)
+    acoustic_half_A(st, op, b, 0.5 * dt, pml, mem)
 
 
 _SIG = {(1, 1): "s11", (2, 2): "s22", (3, 3): "s33", (1, 2): "s12", (2, 1): "s12", (1, 3): "s13",
@@ -208,6 +277,13 @@ class Simulation:
             self.lam, self.mu, self.b = elastic_moduli(vp, vs, rho)
             self.moduli = (self.lam, self.mu)
         self.src = Source(w.src_index, w.src_kinds, w.f0, w.t0, w.amp, w.h, w.shape) if w.src_kinds else None
+        self.pml, self.mem = None, None
+        if getattr(w, "pml_width", 0) > 0:
+            if w.physics != "acoustic":
+                raise NotImplementedError("elastic PML")
+            self.pml = PML(w.n, w.h, w.pml_width, w.pml_R, w.pml_kmax, w.f0, float(np.max(vp)))
+            comps = (1, 3) if w.dim == 2 else (1, 2, 3)
+            self.mem = {f"{k}{c}": np.zeros(w.shape) for k in ("psi", "phi") for c in comps}
         self.state = zero_state(w.physics, w.shape) if state is None else {k: np.array(v, dtype=np.float64) for k, v in state.items()}
         self.step_index = 0
         self.traces = {k: [] for k in w.receivers}
@@ -217,7 +293,7 @@ class Simulation:
         for _ in range(count):
             t_n = self.step_index * w.dt
             if w.physics == "acoustic":
-                acoustic_step(self.state, self.op, self.kappa, self.b, w.dt, t_n, self.src)
+                acoustic_step(self.state, self.op, self.kappa, self.b, w.dt, t_n, self.src, self.pml, self.mem)
             else:
                 elastic_step(self.state, self.op, self.lam, self.mu, self.b, w.dt, t_n, self.src)
             self.step_index += 1

@@ -1,0 +1,134 @@
+// Host-side state of a LOSS handle and the internal functions shared by the host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/loss.h"
+#include "loss_types.h"
+
+namespace lossk {
+
+constexpr int kTableLen = 64;
+
+// One independent grid (shot).  Internal axis slots: 0 = z, 1 = y, 2 = x; 2-D grids have a y extent of 1.
+// Device arrays use a padded layout: x pitch px (multiple of 32 elements), y stride sy = px, z stride sz.
+struct Shot {
+  loss_grid_desc_t d{};
+  int dim = 0;
+  int64_t n[3] = {0, 0, 0};
+  int p[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  int64_t len[3] = {1, 1, 1};
+  int64_t px = 0, sy = 0, sz = 0, total = 0, dense = 0;
+  size_t esize = 8;
+  bool kahan = false;
+  int nfields = 0;
+  void* field[LOSS_NUM_FIELDS] = {};
+  void* comp[LOSS_NUM_FIELDS] = {};
+  void* model[3] = {};   // acoustic: kappa, b; elastic: lambda, mu, b
+  void* tmp[8] = {};     // derivative temporaries (acoustic: tmp[0] = d_z v3)
+  double* W[3] = {};     // PMBC weights per axis slot, scaled by h/3
+  bool has_model = false;
+  double vmax = 0.0;
+  // source
+  bool src_on = false;
+  uint32_t src_kinds = 0;
+  int64_t src_idx[3] = {0, 0, 0};
+  double src_amp = 0, src_f0 = 0, src_t0 = 0, src_norm = 0;
+  double src_g[25] = {};
+  // receivers
+  std::vector<int64_t> rcv[LOSS_NUM_FIELDS];
+  std::vector<int64_t> rcv_offsets;
+  int64_t* rcv_idx = nullptr;  // padded offsets, all fields concatenated
+  int64_t n_rcv = 0;
+  void* traces = nullptr;
+  int64_t trace_cap = 0, rcv_steps = 0;
+  // absorbing ADE-PML layer
+  bool pml_on = false;
+  int pml_width = 0;
+  double pml_R = 1e-6, pml_kmax = 1.0, pml_f0 = 0.0;
+  void* pml_tab[3][3] = {};  // [axis slot][0: tau = dt, 1: dt/2, 2: -dt/2], each [4][n+1] in working precision
+  void* psi[3] = {};         // memory variables of the velocity sub-step, per derivative axis slot
+  void* phi[3] = {};         // memory variables of the stress sub-step
+  // time stepping
+  int64_t step = 0;
+  bool staggered = false;  // velocities hold v at t_step + dt/2 instead of t_step
+};
+
+}  // namespace lossk
+
+struct loss_ctx {
+  std::vector<lossk::Shot> shots;
+  cudaStream_t stream = nullptr;
+  loss_allocator_t alloc{};
+  bool has_alloc = false;
+  std::vector<void*> owned;
+  std::string err;
+  loss_status_t sticky = LOSS_OK;
+  int device = 0;
+  int smem_optin = 0;
+  int num_sms = 0;
+  double* t64 = nullptr;
+  float* t32 = nullptr;
+  // launch accounting (loss_profile / loss_profile_read)
+  int64_t launches[LOSS_NUM_KERNELS] = {};
+  bool prof = false;
+  struct Ev {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> events;
+};
+
+namespace lossk {
+
+// loss_api.cu
+loss_status_t cuda_check(loss_ctx* h, cudaError_t e, const char* what);
+loss_status_t dev_alloc(loss_ctx* h, size_t bytes, void** out);
+void dev_free(loss_ctx* h, void* p);
+loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc, int* threads,
+                        int nbuf);
+bool field_used(const Shot& s, int f);
+bool is_velocity(int f);
+loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows);
+loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d1, void* d2, double* phi, int mem);
+std::vector<double> pmbc_weights_scaled(int n, int p, int n_nb);
+void thomas_tables(std::vector<double>& t64, std::vector<float>& t32);
+
+// Counts one launch of `kernel` and, when profiling is on, brackets it with CUDA events on the stream.
+struct LaunchScope {
+  loss_ctx* h;
+  int kernel;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(loss_ctx* hh, int k) : h(hh), kernel(k) {
+    ++h->launches[k];
+    if (h->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, h->stream);
+  }
+  ~LaunchScope() {
+    if (a && b) {
+      cudaEventRecord(b, h->stream);
+      h->events.push_back({kernel, a, b});
+    }
+  }
+};
+
+// loss_step.cu
+loss_status_t step_shot(loss_ctx* h, Shot& s);
+loss_status_t unstagger(loss_ctx* h, Shot& s);
+
+// kernels
+size_t smem_bytes(const LineGeom& g, int nbuf, size_t esize);
+template <typename T>
+cudaError_t launch_deriv(const DerivArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_x(const AcXArgs<T>& a, int logc, int threads, cudaStream_t st);
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_z(const AcZArgs<T>& a, int logc, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, cudaStream_t st);
+
+}  // namespace lossk

@@ -1,0 +1,159 @@
+// Time-stepping schedule (paper Sec. 3.3): Strang splitting "half A, full B, half A" with the velocity
+// sub-step A and the stress sub-step B.  Between steps the velocities are kept half a step ahead (staggered),
+// which merges the trailing half A of one step with the leading half A of the next; the state is brought back
+// to the integer time level (v_n = v_{n+1/2} + dt/2 b grad sigma_n) whenever velocities are read.
+#include <cmath>
+
+#include "loss_host.h"
+
+namespace lossk {
+
+#define LOSS_TRY(expr)              \
+  do {                              \
+    loss_status_t st_ = (expr);     \
+    if (st_ != LOSS_OK) return st_; \
+  } while (0)
+
+static double ricker(double t, double f0, double t0) {
+  const double a = (M_PI * f0 * (t - t0)) * (M_PI * f0 * (t - t0));
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// 2-D acoustic.
+template <typename T>
+static PmlAxis<T> pml_axis(const Shot& s, int k, double tau) {
+  const int v = (tau == s.d.dt) ? 0 : (tau > 0 ? 1 : 2);
+  return PmlAxis<T>{(const T*)s.pml_tab[k][v], s.pml_width, (int)s.n[k]};
+}
+
+template <typename T, bool K>
+static loss_status_t ac_x(loss_ctx* h, Shot& s, int do_B, double acoef, double src_amp) {
+  LineGeom g;
+  int logc, threads;
+  LOSS_TRY(line_geom(h, s, 2, s.sz, s.sy, &g, &logc, &threads, 3));
+  AcXArgs<T> a{};
+  a.g = g;
+  a.tb = Tables{s.W[2], h->t32, h->t64};
+  a.sigma = (T*)s.field[LOSS_FIELD_SIGMA];
+  a.v1 = (T*)s.field[LOSS_FIELD_V1];
+  a.kappa = (const T*)s.model[0];
+  a.b = (const T*)s.model[1];
+  a.tmp = (const T*)s.tmp[0];
+  a.csig = (T*)s.comp[LOSS_FIELD_SIGMA];
+  a.cv1 = (T*)s.comp[LOSS_FIELD_V1];
+  a.dt = (T)s.d.dt;
+  a.acoef = (T)acoef;
+  a.s3h = (T)(3.0 / s.h[2]);
+  a.minf = (T)(2.0 - std::sqrt(3.0));
+  a.do_B = do_B;
+  a.src.on = (do_B && s.src_on && src_amp != 0.0) ? 1 : 0;
+  a.src.zs = (int)s.src_idx[0];
+  a.src.ys = 0;
+  a.src.xs = (int)s.src_idx[2];
+  a.src.amp = src_amp;
+  for (int i = 0; i < 25; ++i) a.src.g[i] = s.src_g[i];
+  a.pml = s.pml_on ? 1 : 0;
+  if (s.pml_on) {
+    a.xA = pml_axis<T>(s, 2, acoef);
+    a.xB = pml_axis<T>(s, 2, s.d.dt);
+    a.zB = pml_axis<T>(s, 0, s.d.dt);
+    a.psix = (T*)s.psi[2];
+    a.phix = (T*)s.phi[2];
+    a.phiz = (T*)s.phi[0];
+  }
+  LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
+  return cuda_check(h, launch_ac_x<T, K>(a, logc, threads, h->stream), "acoustic x kernel");
+}
+
+template <typename T, bool K>
+static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
+  LineGeom g;
+  int logc, threads;
+  LOSS_TRY(line_geom(h, s, 0, s.sz, s.sy, &g, &logc, &threads, 2));
+  AcZArgs<T> a{};
+  a.g = g;
+  a.tb = Tables{s.W[0], h->t32, h->t64};
+  a.sigma = (const T*)s.field[LOSS_FIELD_SIGMA];
+  a.v3 = (T*)s.field[LOSS_FIELD_V3];
+  a.b = (const T*)s.model[1];
+  a.tmp = (T*)s.tmp[0];
+  a.cv3 = (T*)s.comp[LOSS_FIELD_V3];
+  a.acoef = (T)acoef;
+  a.s3h = (T)(3.0 / s.h[0]);
+  a.minf = (T)(2.0 - std::sqrt(3.0));
+  a.do_tmp = do_tmp;
+  a.pml = s.pml_on ? 1 : 0;
+  if (s.pml_on) {
+    a.zA = pml_axis<T>(s, 0, acoef);
+    a.psiz = (T*)s.psi[0];
+  }
+  LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_Z);
+  return cuda_check(h, launch_ac_z<T, K>(a, logc, threads, h->stream), "acoustic z kernel");
+}
+
+template <typename T>
+static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mode) {
+  if (s.n_rcv == 0) return LOSS_OK;
+  T* row = (T*)s.traces + (size_t)s.rcv_steps * s.n_rcv;
+  for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {
+    const int64_t off = s.rcv_offsets[f], cnt = s.rcv_offsets[f + 1] - off;
+    if (cnt == 0 || is_velocity(f) != velocities) continue;
+    LaunchScope ls(h, LOSS_KERNEL_GATHER);
+    LOSS_TRY(cuda_check(h, launch_gather<T>((const T*)s.field[f], s.rcv_idx + off, cnt, row + off, mode, h->stream),
+                        "receiver gather"));
+  }
+  return LOSS_OK;
+}
+
+template <typename T, bool K>
+static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
+  const double dt = s.d.dt;
+  if (!s.staggered) {
+    LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * dt, 0.0)));
+    LOSS_TRY((ac_z<T, K>(h, s, 0.5 * dt, 1)));
+    s.staggered = true;
+  }
+  LOSS_TRY(gather_fields<T>(h, s, true, 0));  // v at t_{n+1/2}
+  double amp = 0.0;
+  if (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE))
+    amp = dt * s.src_norm * ricker((double)s.step * dt + 0.5 * dt, s.src_f0, s.src_t0);
+  LOSS_TRY((ac_x<T, K>(h, s, 1, dt, amp)));
+  LOSS_TRY((ac_z<T, K>(h, s, dt, 1)));
+  LOSS_TRY(gather_fields<T>(h, s, true, 1));   // (v_{n+1/2} + v_{n+3/2}) / 2 = v_{n+1}
+  LOSS_TRY(gather_fields<T>(h, s, false, 0));  // sigma_{n+1}
+  if (s.n_rcv) ++s.rcv_steps;
+  ++s.step;
+  return LOSS_OK;
+}
+
+template <typename T, bool K>
+static loss_status_t acoustic2d_unstagger(loss_ctx* h, Shot& s) {
+  const double dt = s.d.dt;
+  LOSS_TRY((ac_x<T, K>(h, s, 0, -0.5 * dt, 0.0)));
+  LOSS_TRY((ac_z<T, K>(h, s, -0.5 * dt, 0)));
+  s.staggered = false;
+  return LOSS_OK;
+}
+
+loss_status_t step_shot(loss_ctx* h, Shot& s) {
+  if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {
+    if (s.esize == 8) return acoustic2d_step<double, false>(h, s);
+    if (s.kahan) return acoustic2d_step<float, true>(h, s);
+    return acoustic2d_step<float, false>(h, s);
+  }
+  h->err = "time stepping of this physics/dimension is not built";
+  return LOSS_E_UNSUPPORTED;
+}
+
+loss_status_t unstagger(loss_ctx* h, Shot& s) {
+  if (!s.staggered) return LOSS_OK;
+  if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {
+    if (s.esize == 8) return acoustic2d_unstagger<double, false>(h, s);
+    if (s.kahan) return acoustic2d_unstagger<float, true>(h, s);
+    return acoustic2d_unstagger<float, false>(h, s);
+  }
+  return LOSS_E_UNSUPPORTED;
+}
+
+}  // namespace lossk

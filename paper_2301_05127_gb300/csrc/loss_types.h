@@ -1,0 +1,121 @@
+// Launch descriptors shared by the host runtime (loss_api.cu) and the kernels (loss_kernels*.cu).
+// Plain structs passed by value as kernel parameters.
+#pragma once
+
+#include <cstdint>
+
+namespace lossk {
+
+// How one thread block's bundle of whole lines along one axis maps to a field array.
+//   X flavour: lines along the contiguous axis; bundle b holds rows r = b*L .. b*L + L - 1 of the flattened
+//              (z, y) row index; row r starts at (r / ny1) * sz + (r % ny1) * sy.
+//   S flavour: lines along a strided axis; bundle b = outer * nxb + xb holds the L neighbouring x positions
+//              x0 = xb * L ..; line l starts at outer * so + x0 + l and steps by pstride.
+struct LineGeom {
+  int n;       // intervals along the axis (n + 1 points per line)
+  int p, M;    // patches and patch length
+  int NC;      // chunks per patch
+  int n_nb;    // PMBC halo width
+  int L;       // lines per bundle
+  int pitch;   // shared-memory pitch (X: per line, S: per position)
+  int buf;     // elements per shared-memory line buffer
+  int nbundles;
+  // X flavour
+  int ny1;
+  int64_t sz, sy;
+  int64_t nrows;
+  // S flavour
+  int nx1, nxb;
+  int64_t so, pstride;
+};
+
+struct Tables {
+  const double* W;    // PMBC weights [(p+1)][2 n_nb + 1], scaled by h/3
+  const float* t32;   // Thomas factors m_j, j < 64
+  const double* t64;
+};
+
+template <typename T>
+struct DerivArgs {
+  LineGeom g;
+  Tables tb;
+  const T* f;
+  T* d1;
+  T* d2;
+  double* phi_out;
+  T s1;     // 3 / h
+  double s1d;  // 3 / h in double (phi output)
+  T s2;     // 6 / h^2
+  T minf;   // 2 - sqrt(3)
+  int lines_per_outer;  // S flavour: lines per outer index in the phi_out ordering (= nx1)
+};
+
+struct SourceArgs {
+  int on;
+  int zs, ys, xs;    // centre
+  double amp;        // dt * amp * f_r(t) / (sum of profile * cell volume), or 0
+  double g[25];      // exp(-o^2 / 8), o = -12..12
+};
+
+// Exponential-flow coefficients of the ADE-PML along one axis for one step length tau (paper Sec. 3.3):
+// tab[0][i] = E = exp(-beta tau), tab[1][i] = (d/k^2)(1 - E)/beta, tab[2][i] = 1/beta,
+// tab[3][i] = tau alpha / (d + alpha k), for i = 0..n; points with i < width or i > n - width are in the layer.
+template <typename T>
+struct PmlAxis {
+  const T* tab;
+  int width;
+  int n;
+  __device__ __forceinline__ bool in(int i) const { return i < width || i > n - width; }
+  // Advance the memory variable over tau with frozen derivative g; return the field increment factor.
+  __device__ __forceinline__ T step(T* mem, int64_t gi, int i, T g) const {
+    const int n1 = n + 1;
+    const T m0 = mem[gi];
+    const T m1 = tab[i] * m0 - tab[n1 + i] * g;
+    mem[gi] = m1;
+    return tab[2 * n1 + i] * (m1 - m0) - tab[3 * n1 + i] * g;
+  }
+};
+
+template <typename T>
+struct AcXArgs {
+  LineGeom g;
+  Tables tb;
+  T* sigma;
+  T* v1;
+  const T* kappa;
+  const T* b;        // buoyancy 1/rho
+  const T* tmp;      // d_z v3 at the current half step (read when do_B)
+  T* csig;           // Kahan compensation (KAHAN only)
+  T* cv1;
+  T dt;              // B step length
+  T acoef;           // A step length (dt, dt/2 or -dt/2)
+  T s3h;             // 3 / h_x
+  T minf;
+  int do_B;
+  SourceArgs src;
+  int pml;
+  PmlAxis<T> xA, xB, zB;  // x layer for the A step length, x and z layers for tau = dt (B)
+  T* psix;
+  T* phix;
+  T* phiz;
+};
+
+template <typename T>
+struct AcZArgs {
+  LineGeom g;
+  Tables tb;
+  const T* sigma;
+  T* v3;
+  const T* b;
+  T* tmp;            // out: d_z v3 after the update (when do_tmp)
+  T* cv3;
+  T acoef;
+  T s3h;             // 3 / h_z
+  T minf;
+  int do_tmp;
+  int pml;
+  PmlAxis<T> zA;
+  T* psiz;
+};
+
+}  // namespace lossk

@@ -45,6 +45,9 @@ class Workload:
     precision: str = "fp64"
     checkpoint_every: int = 0
     seed: int = 0
+    pml_width: int = 0  # points of the absorbing ADE-PML layer on each side of every axis (0 = none)
+    pml_R: float = 1e-6  # theoretical reflection coefficient
+    pml_kmax: float = 1.0
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -79,8 +82,9 @@ def _top_row_receivers(shape) -> np.ndarray:
     return np.arange(int(np.prod(shape[1:])), dtype=np.int64)
 
 
-def acoustic2d_small(n: int = 128, p: int = 2, steps: int = 300, n_nb: int = 12) -> Workload:
-    """2-D acoustic, constant v = 2000 m/s, rho = 1000 kg/m^3, h = 10 m, Ricker 15 Hz at the centre, FP64."""
+def acoustic2d_small(n: int = 128, p: int = 2, steps: int = 300, n_nb: int = 12, pml_width: int = 20) -> Workload:
+    """2-D acoustic, constant v = 2000 m/s, rho = 1000 kg/m^3, h = 10 m, Ricker 15 Hz at the centre, FP64, with
+    an absorbing ADE-PML layer of ``pml_width`` points on every side."""
     shape = (n + 1, n + 1)
     h = 10.0
 
@@ -92,7 +96,7 @@ def acoustic2d_small(n: int = 128, p: int = 2, steps: int = 300, n_nb: int = 12)
         name=f"acoustic2d_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h), n_nb=n_nb,
         dt=_cfl_dt(h, 2000.0), steps=steps, model_fn=model, src_index=(n // 2, n // 2),
         src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
-        receivers={"sigma": _top_row_receivers(shape)}, precision="fp64")
+        receivers={"sigma": _top_row_receivers(shape)}, precision="fp64", pml_width=pml_width)
 
 
 def _layered_velocity_2d(n: int, seed: int) -> np.ndarray:
@@ -106,7 +110,7 @@ def _layered_velocity_2d(n: int, seed: int) -> np.ndarray:
 
 
 def acoustic2d_layered(n: int = 2048, p: int = 8, steps: int = 2000, n_nb: int = 20,
-                       precision: str = "fp32_kahan", seed: int = 2002) -> Workload:
+                       precision: str = "fp32_kahan", seed: int = 2002, pml_width: int = 40) -> Workload:
     """2-D acoustic three-layer model with a 5 % Gaussian-correlated perturbation, Ricker 20 Hz at the centre."""
     shape = (n + 1, n + 1)
     h = 10.0
@@ -121,7 +125,7 @@ def acoustic2d_layered(n: int = 2048, p: int = 8, steps: int = 2000, n_nb: int =
         name=f"acoustic2d_layered_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h),
         n_nb=n_nb, dt=_cfl_dt(h, vmax), steps=steps, model_fn=model, src_index=(n // 2, n // 2),
         src_kinds=("pressure",), f0=f0, t0=1.2 / f0, receivers={"sigma": _top_row_receivers(shape)},
-        precision=precision, seed=seed)
+        precision=precision, seed=seed, pml_width=pml_width)
 
 
 def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int = 20,
@@ -198,7 +202,8 @@ def batched_shots(n_shots: int = 64, steps: int = 1500, n_nb: int = 20, seed: in
             name=f"shot{s}_{n}", dim=2, physics="acoustic", n=(n, n), p=(n // M, n // M), h=(h, h),
             n_nb=n_nb, dt=_cfl_dt(h, float(v_layers.max())), steps=steps, model_fn=model,
             src_index=(5, n // 2), src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
-            receivers={"sigma": _top_row_receivers(shape)}, precision=precision, seed=seed + 1 + s))
+            receivers={"sigma": _top_row_receivers(shape)}, precision=precision, seed=seed + 1 + s,
+            pml_width=40))
     return out
 
 
@@ -219,7 +224,8 @@ def gaussian_pulse_2d(n: int, p: int, n_nb: int = 20, dt: float = 1e-4, steps: i
     return w, sigma0
 
 
-def scaled(w: Workload, n: int, p: int, steps: int, n_nb: Optional[int] = None) -> Workload:
+def scaled(w: Workload, n: int, p: int, steps: int, n_nb: Optional[int] = None,
+           pml_width: Optional[int] = None) -> Workload:
     """A smaller copy of an acoustic/elastic workload on an n-interval grid (same physics, h, dt, source
     type), used for parity cases that the oracle finishes in seconds.  Models are rebuilt at the new size
     with the same recipe (constant or freshly seeded)."""
@@ -239,7 +245,8 @@ def scaled(w: Workload, n: int, p: int, steps: int, n_nb: Optional[int] = None) 
     rec = {k: np.arange(int(np.prod(shape[1:])), dtype=np.int64) for k in w.receivers}
     return dataclasses.replace(
         w, name=f"{w.name}_as{n}_p{p}", n=(n,) * d, p=(p,) * d, steps=steps, model_fn=model,
-        n_nb=w.n_nb if n_nb is None else n_nb, src_index=tuple(n // 2 for _ in range(d)), receivers=rec)
+        n_nb=w.n_nb if n_nb is None else n_nb, src_index=tuple(n // 2 for _ in range(d)), receivers=rec,
+        pml_width=w.pml_width if pml_width is None else pml_width)
 
 
 WORKLOADS = {
