@@ -195,6 +195,21 @@ loss_status_t loss_profile(loss_handle_t handle, int32_t enable);
  * duration in milliseconds (waits for the stream).  kernel = -1 gives the totals over all kernels. */
 loss_status_t loss_profile_read(loss_handle_t handle, int32_t kernel, double* total_ms, int64_t* launches);
 
+/* First LOSS derivative along `axis` for callers that cannot allocate device memory (code running under another
+ * framework's allocator or memory budget, or inside a stream capture where cudaMalloc is not allowed), so they
+ * cannot create a handle.  The paper has no counterpart: this is a deployment variant of loss_derivative.
+ * desc: the grid (same rules as loss_create_grid; physics and dt are ignored); f, d1: DEVICE pointers to dense
+ * arrays of the grid shape in the working precision of desc->precision; cuda_stream: the stream to run on.
+ * Nothing is allocated: the PMBC weights and Thomas factors are written into a 64 KiB static device array that
+ * every GPU loading this library keeps until the process exits.  Limit: (p + 1) * (2 n_nb + 1) <= 8096 on the
+ * axis, else LOSS_E_UNSUPPORTED before any work is queued.  Every call rewrites the whole table it reads, so no
+ * state carries over between calls, but calls that overlap on the GPU (other streams or devices sharing a
+ * context) race on the array: serialise them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.
+ * Returns LOSS_E_ARG / LOSS_E_SHAPE for bad arguments, LOSS_E_CUDA if a CUDA call fails. */
+loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis, const void* f, void* d1,
+                                      void* cuda_stream);
+
 /* Wait for all work queued on the handle's stream. */
 loss_status_t loss_sync(loss_handle_t handle);
 

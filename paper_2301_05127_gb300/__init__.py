@@ -69,6 +69,7 @@ _PROTOS = {
     "loss_set_state": (_I32, [_H, _P, ctypes.c_size_t]),
     "loss_get_step": (_I32, [_H, _I32, ctypes.POINTER(_I64)]),
     "loss_sync": (_I32, [_H]),
+    "loss_derivative_noalloc": (_I32, [ctypes.POINTER(GridDesc), _I32, _P, _P, _P]),
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }

@@ -262,7 +262,7 @@ static void source_setup(Shot& s) {
 
 // ----------------------------------------------------------------------------------------------------------------
 // Shot setup.
-static loss_status_t validate(const loss_grid_desc_t& d, std::string* why) {
+loss_status_t validate(const loss_grid_desc_t& d, std::string* why) {
   if (d.dim != 2 && d.dim != 3) return *why = "dim must be 2 or 3", LOSS_E_SHAPE;
   if (d.physics != LOSS_ACOUSTIC && d.physics != LOSS_ELASTIC) return *why = "unknown physics", LOSS_E_ARG;
   if (d.precision != LOSS_FP64 && d.precision != LOSS_FP32 && d.precision != LOSS_FP32_KAHAN)
@@ -284,7 +284,7 @@ static loss_status_t validate(const loss_grid_desc_t& d, std::string* why) {
   return LOSS_OK;
 }
 
-static loss_status_t setup_shot(loss_ctx* h, Shot& s) {
+void shot_geometry(Shot& s) {
   const loss_grid_desc_t& d = s.d;
   s.dim = d.dim;
   // internal slots: 0 = z, 1 = y, 2 = x
@@ -313,6 +313,11 @@ static loss_status_t setup_shot(loss_ctx* h, Shot& s) {
   s.sz = s.px * s.len[1];
   s.total = s.sz * s.len[0];
   s.dense = s.len[0] * s.len[1] * s.len[2];
+}
+
+static loss_status_t setup_shot(loss_ctx* h, Shot& s) {
+  const loss_grid_desc_t& d = s.d;
+  shot_geometry(s);
   const size_t fb = (size_t)s.total * s.esize;
   s.nfields = d.physics == LOSS_ELASTIC ? 9 : 4;  // acoustic uses V1, V2 (3-D), V3, SIGMA(=3)
   for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {

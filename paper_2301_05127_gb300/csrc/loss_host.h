@@ -92,6 +92,8 @@ void dev_free(loss_ctx* h, void* p);
 loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc, int* threads,
                         int nbuf);
 bool field_used(const Shot& s, int f);
+void shot_geometry(Shot& s);
+loss_status_t validate(const loss_grid_desc_t& d, std::string* why);
 bool is_velocity(int f);
 loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows);
 loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d1, void* d2, double* phi, int mem);
