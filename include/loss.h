@@ -187,6 +187,12 @@ enum {
   LOSS_NUM_KERNELS = 16
 };
 
+/* Launch shape of one kernel family of the handle: lines_per_block = number of whole grid lines one thread block
+ * holds on chip (power of two, 1..32) and chunk_log2 = log2 of the number of unknowns one thread solves serially
+ * (3 or 4; FP64 grids always use 4); 0 = the built-in choice.  Applies to every shot; shapes that do not fit
+ * fall back to smaller bundles at launch.  Used by the autotuner. */
+loss_status_t loss_set_launch(loss_handle_t handle, int32_t kernel, int32_t lines_per_block, int32_t chunk_log2);
+
 /* Reset the per-kernel counters of the handle and switch CUDA-event timing of every kernel launch on
  * (enable != 0) or off.  Launches are always counted. */
 loss_status_t loss_profile(loss_handle_t handle, int32_t enable);

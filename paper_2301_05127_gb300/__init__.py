@@ -70,6 +70,7 @@ _PROTOS = {
     "loss_get_step": (_I32, [_H, _I32, ctypes.POINTER(_I64)]),
     "loss_sync": (_I32, [_H]),
     "loss_derivative_noalloc": (_I32, [ctypes.POINTER(GridDesc), _I32, _P, _P, _P]),
+    "loss_set_launch": (_I32, [_H, _I32, _I32, _I32]),
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
@@ -303,6 +304,10 @@ class Grid:
         s = _I64()
         _check(lib().loss_get_step(self.h, shot, ctypes.byref(s)), self.h)
         return s.value
+
+    def set_launch(self, kernel, lines_per_block=0, chunk_log2=0):
+        kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        _check(lib().loss_set_launch(self.h, kid, int(lines_per_block), int(chunk_log2)), self.h)
 
     def profile(self, enable: bool = True):
         _check(lib().loss_profile(self.h, 1 if enable else 0), self.h)

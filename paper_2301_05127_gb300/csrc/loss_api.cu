@@ -167,8 +167,10 @@ static int axis_slot(const Shot& s, int axis) {
 }
 
 // Build the launch geometry of lines along internal slot `k` for an array with strides (sz, sy, 1).
+// nbuf padded line buffers and nstage dense row-staging buffers (X flavour) per block; want_L > 0 requests a
+// bundle width (lines per block).
 loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc,
-                        int* threads, int nbuf) {
+                        int* threads, int nbuf, int nstage, int want_L, int want_logc) {
   const int n = (int)s.n[k];
   const int p = s.p[k];
   const int M = n / p;
@@ -176,17 +178,25 @@ loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t s
   G.n = n;
   G.p = p;
   G.M = M;
-  *logc = (M >= 96) ? 5 : 4;
+  // Chunk length: 8 for FP32 lines along x (more threads per line, shorter serial chains), else 16 (the
+  // Thomas factors reach their limit to double rounding within 16 positions).
+  *logc = (k == 2 && s.esize == 4) ? 3 : 4;
+  if (want_logc >= 3 && want_logc <= 4 && !(s.esize == 8 && want_logc == 3)) *logc = want_logc;
   const int C = 1 << *logc;
   G.NC = (M - 1 + C - 1) / C;
   G.n_nb = s.d.n_nb;
+  G.mmagic = (unsigned)((((uint64_t)1 << 32) + (uint64_t)M - 1) / (uint64_t)M);
   const int per_line = p * G.NC;
   const size_t es = s.esize;
-  const size_t smax = (size_t)h->smem_optin;
+  const size_t smax = (size_t)h->smem_optin - 2048;  // headroom for the kernels' static shared memory
   const int np_pad = (n + (n >> *logc)) + 1;  // padpos(n) + 1
+  const int vec = (int)(16 / es);
+  G.spitch = ((n + 1 + vec - 1) / vec) * vec;
   if (k == 2) {
     // X flavour: rows of the flattened (z, y) index.
-    int L = std::max(1, std::min(32, 256 / std::max(1, per_line)));
+    int L = 1;
+    while (L < 32 && 2 * L * per_line <= 256) L *= 2;
+    if (want_L > 0 && want_L <= 32 && want_L * per_line <= (es == 8 ? 512 : 1024)) L = want_L;
     while (true) {
       int pitch = np_pad;
       const int want = per_line % 32;
@@ -196,7 +206,8 @@ loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t s
       G.L = L;
       G.pitch = pitch;
       G.buf = L * pitch;
-      if (smem_bytes(G, nbuf, es) <= smax || L == 1) break;
+      G.stage = nstage ? L * G.spitch : 0;
+      if (smem_bytes(G, nbuf, nstage, es) <= smax || L == 1) break;
       L = std::max(1, L / 2);
     }
     G.ny1 = (int)s.len[1];
@@ -206,18 +217,20 @@ loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t s
     G.nbundles = (int)((G.nrows + G.L - 1) / G.L);
     G.pstride = 1;
   } else {
-    // S flavour: bundles of neighbouring x lines.
-    int L = 32;
+    // S flavour: bundles of neighbouring x lines (nstage must be 0).
+    int L = (want_L > 0 && want_L <= 32) ? want_L : (es == 8 ? 4 : 8);
     while (L > 1) {
       G.L = L;
       G.pitch = L;
       G.buf = np_pad * L;
-      if (smem_bytes(G, nbuf, es) <= smax && L * per_line <= 1024) break;
+      G.stage = 0;
+      if (smem_bytes(G, nbuf, 0, es) <= smax && L * per_line <= (es == 8 ? 512 : 1024)) break;
       L /= 2;
     }
     G.L = L;
     G.pitch = L;
     G.buf = np_pad * L;
+    G.stage = 0;
     G.nx1 = (int)s.len[2];
     G.nxb = (G.nx1 + L - 1) / L;
     if (k == 0) {
@@ -230,11 +243,14 @@ loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t s
       G.nbundles = (int)(s.len[0] * G.nxb);
     }
   }
-  if (smem_bytes(G, nbuf, es) > smax)
+  if (smem_bytes(G, nbuf, nstage, es) > smax)
     return fail(h, LOSS_E_UNSUPPORTED,
                 "grid line of " + std::to_string(n + 1) + " points does not fit in shared memory");
   const int work = G.L * per_line;
-  *threads = std::min(1024, ((work + 31) / 32) * 32);
+  const int max_threads = (es == 8) ? 512 : 1024;
+  if (work > max_threads)
+    return fail(h, LOSS_E_UNSUPPORTED, "grid line of " + std::to_string(n + 1) + " points needs more than 1024 chunks");
+  *threads = ((work + 31) / 32) * 32;
   *g = G;
   return LOSS_OK;
 }
@@ -460,6 +476,17 @@ loss_status_t loss_destroy(loss_handle_t h) {
   return LOSS_OK;
 }
 
+loss_status_t loss_set_launch(loss_handle_t h, int32_t kernel, int32_t lines_per_block, int32_t chunk_log2) {
+  LOSS_TRY(guard(h));
+  if (chunk_log2 != 0 && chunk_log2 != 3 && chunk_log2 != 4) return fail(h, LOSS_E_ARG, "chunk_log2 must be 0, 3 or 4");
+  if (kernel < 0 || kernel >= LOSS_NUM_KERNELS) return fail(h, LOSS_E_ARG, "kernel id out of range");
+  if (lines_per_block < 0 || lines_per_block > 32 || (lines_per_block & (lines_per_block - 1)))
+    return fail(h, LOSS_E_ARG, "lines_per_block must be 0 or a power of two <= 32");
+  h->lines_per_block[kernel] = lines_per_block;
+  h->chunk_log2[kernel] = chunk_log2;
+  return LOSS_OK;
+}
+
 loss_status_t loss_profile(loss_handle_t h, int32_t enable) {
   LOSS_TRY(guard(h));
   LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
@@ -540,6 +567,9 @@ loss_status_t loss_set_model(loss_handle_t h, int32_t shot, const double* vp, co
   }
   s->vmax = 0.0;
   for (int64_t i = 0; i < N; ++i) s->vmax = std::max(s->vmax, std::fabs(pvp[i]));
+  s->b_const = true;
+  for (int64_t i = 1; i < N && s->b_const; ++i) s->b_const = prho[i] == prho[0];
+  s->b0 = 1.0 / prho[0];
   for (int m = 0; m < nm; ++m) {
     if (s->esize == 8) {
       LOSS_TRY(copy_in(h, *s, s->model[m], md[m].data(), LOSS_MEM_HOST));
@@ -900,7 +930,8 @@ static loss_status_t run_derivative_t(loss_ctx* h, Shot& s, int k, const T* f, T
   const int64_t sy = s.len[2], sz = s.len[2] * s.len[1];
   LineGeom g;
   int logc, threads;
-  LOSS_TRY(line_geom(h, s, k, sz, sy, &g, &logc, &threads, d2 ? 3 : 2));
+  LOSS_TRY(line_geom(h, s, k, sz, sy, &g, &logc, &threads, d2 ? 3 : 2, 0, h->lines_per_block[LOSS_KERNEL_DERIVATIVE],
+                     h->chunk_log2[LOSS_KERNEL_DERIVATIVE]));
   DerivArgs<T> a{};
   a.g = g;
   a.tb = tables_for<T>(h, s, k);

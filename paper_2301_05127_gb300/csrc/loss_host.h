@@ -33,6 +33,8 @@ struct Shot {
   double* W[3] = {};     // PMBC weights per axis slot, scaled by h/3
   bool has_model = false;
   double vmax = 0.0;
+  bool b_const = false;  // density constant: buoyancy passed as a scalar, the b array is not read
+  double b0 = 0.0;
   // source
   bool src_on = false;
   uint32_t src_kinds = 0;
@@ -73,6 +75,8 @@ struct loss_ctx {
   int num_sms = 0;
   double* t64 = nullptr;
   float* t32 = nullptr;
+  int lines_per_block[LOSS_NUM_KERNELS] = {};  // 0 = built-in choice (loss_set_launch)
+  int chunk_log2[LOSS_NUM_KERNELS] = {};
   // launch accounting (loss_profile / loss_profile_read)
   int64_t launches[LOSS_NUM_KERNELS] = {};
   bool prof = false;
@@ -90,7 +94,7 @@ loss_status_t cuda_check(loss_ctx* h, cudaError_t e, const char* what);
 loss_status_t dev_alloc(loss_ctx* h, size_t bytes, void** out);
 void dev_free(loss_ctx* h, void* p);
 loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc, int* threads,
-                        int nbuf);
+                        int nbuf, int nstage, int want_L, int want_logc);
 bool field_used(const Shot& s, int f);
 void shot_geometry(Shot& s);
 loss_status_t validate(const loss_grid_desc_t& d, std::string* why);
@@ -123,7 +127,7 @@ loss_status_t step_shot(loss_ctx* h, Shot& s);
 loss_status_t unstagger(loss_ctx* h, Shot& s);
 
 // kernels
-size_t smem_bytes(const LineGeom& g, int nbuf, size_t esize);
+size_t smem_bytes(const LineGeom& g, int nbuf, int nstage, size_t esize);
 template <typename T>
 cudaError_t launch_deriv(const DerivArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
 template <typename T, bool KAHAN>

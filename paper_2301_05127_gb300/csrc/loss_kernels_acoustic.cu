@@ -1,9 +1,9 @@
 // sm_103a kernels of the 2-D acoustic LOSS step and of the stand-alone derivative.
 //
 // Time stepping (paper Sec. 3.3, Strang "half A, full B, half A", with the exponential ADE-PML sub-flows in
-// the absorbing layers).  Consecutive half steps of A
-// share the same stress, so n steps are one half A, n - 1 alternations (full B, full A), a full B and a half
-// A.  The library keeps the velocities half a step ahead between calls (staggered state), so one step is:
+// the absorbing layers).  Consecutive half steps of A share the same stress, so n steps are one half A,
+// n - 1 alternations (full B, full A), a full B and a half A.  The library keeps the velocities half a step
+// ahead between calls (staggered state), so one step is:
 //   X kernel (lines along x):  sigma += -dt kappa (d_x v1 + d_z v3) + source           [sub-step B]
 //                              v1    += -dt b d_x sigma                                   [A, x part]
 //   Z kernel (lines along z):  v3    += -dt b d_z sigma                                   [A, z part]
@@ -11,8 +11,11 @@
 // Inside a PML layer the increments -tau g are replaced by the exact exponential flow of the memory variables
 // (PmlAxis::step): Phi_x, Phi_z advance in the B part of the X kernel, Psi_x in its A part, Psi_z in the Z
 // kernel, each exactly once per sub-step.
-// Each kernel holds whole grid lines (all patches) on chip, so the PMBC halo of every junction is read from
-// shared memory and each field is read from and written to HBM once per kernel.
+//
+// Each block holds whole grid lines (all patches) on chip, so the PMBC halo of every junction is read from
+// shared memory and each field is read from and written to HBM once per kernel.  All global -> shared traffic
+// is issued up front with cp.async in two groups: the lines the first solve needs, then the operands of the
+// pointwise updates, which arrive while the block solves.
 #include <cuda_runtime.h>
 
 #include "loss_line.cuh"
@@ -29,19 +32,26 @@ __device__ __forceinline__ T* align_ptr(void* p) {
   return reinterpret_cast<T*>(u);
 }
 
-// Shared-memory carve-up: nbuf line buffers, two summary arrays, phi, line bases.
+// Shared-memory carve-up: nbuf padded line buffers, nstage dense staging buffers, two summary arrays, phi,
+// line bases.  Must match smem_bytes().
 template <typename T>
 struct Carve {
   T* buf[3];
+  T* stg[4];
   T* sA;
   T* sB;
   double* phi;
   int64_t* lb;
-  __device__ Carve(unsigned char* sm, const LineGeom& g, int nbuf) {
+  __device__ Carve(unsigned char* sm, const LineGeom& g, int nbuf, int nstage) {
     T* p = reinterpret_cast<T*>(sm);
     for (int i = 0; i < 3; ++i) {
       buf[i] = p;
       if (i < nbuf) p += g.buf;
+    }
+    p = align_ptr<T>(p);
+    for (int i = 0; i < 4; ++i) {
+      stg[i] = p;
+      if (i < nstage) p += g.stage;
     }
     const int nw = g.L * g.p * g.NC;
     sA = align_ptr<T>(p);
@@ -71,54 +81,70 @@ __device__ __forceinline__ int bundle_bases(const LineGeom& g, int bundle, int64
   return nvalid;
 }
 
-// Load whole lines of a global field into a shared buffer.
+// Issue cp.async copies of whole lines of a global field into a padded line buffer (no wait).
 template <typename T, bool SFLAV, class BUN>
-__device__ __forceinline__ void load_lines(const T* __restrict__ src, T* dst, const BUN& bun, const LineGeom& g,
-                                           const int64_t* lb, int nvalid) {
+__device__ __forceinline__ void stage_padded(const T* __restrict__ src, T* dst, const BUN& bun, const LineGeom& g,
+                                             const int64_t* lb, int nvalid, int logL) {
   const int np = g.n + 1;
   if (SFLAV) {
-    const int tot = np * g.L;
+    const int tot = np << logL;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int pos = i / g.L;
-      const int l = i - pos * g.L;
-      if (l < nvalid) dst[bun.at(l, pos)] = src[lb[l] + (int64_t)pos * g.pstride];
+      const int pos = i >> logL;
+      const int l = i & (g.L - 1);
+      if (l < nvalid) cp_async<sizeof(T)>(&dst[bun.at(l, pos)], src + lb[l] + (int64_t)pos * g.pstride);
     }
   } else {
-    const int tot = np * nvalid;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int l = i / np;
-      const int pos = i - l * np;
-      dst[bun.at(l, pos)] = src[lb[l] + pos];
-    }
+    for (int l = 0; l < nvalid; ++l)
+      for (int pos = threadIdx.x; pos < np; pos += blockDim.x)
+        cp_async<sizeof(T)>(&dst[bun.at(l, pos)], src + lb[l] + pos);
   }
 }
+
+// Issue 16-byte cp.async copies of whole rows (X flavour) into a dense staging buffer of pitch g.spitch.
+template <typename T>
+__device__ __forceinline__ void stage_rows(const T* __restrict__ src, T* dst, const LineGeom& g, const int64_t* lb,
+                                           int nvalid) {
+  constexpr int V = 16 / sizeof(T);
+  const int nchunks = g.spitch / V;
+  for (int l = 0; l < nvalid; ++l)
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) cp_async<16>(dst + l * g.spitch + c * V, src + lb[l] + c * V);
+}
+
 
 // Iterate (line, pos, global offset) over the bundle in a coalesced order and call fn.
 template <bool SFLAV, class FN>
-__device__ __forceinline__ void for_points(const LineGeom& g, const int64_t* lb, int nvalid, FN fn) {
+__device__ __forceinline__ void for_points(const LineGeom& g, const int64_t* lb, int nvalid, int logL, FN fn) {
   const int np = g.n + 1;
   if (SFLAV) {
-    const int tot = np * g.L;
+    const int tot = np << logL;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int pos = i / g.L;
-      const int l = i - pos * g.L;
+      const int pos = i >> logL;
+      const int l = i & (g.L - 1);
       if (l < nvalid) fn(l, pos, lb[l] + (int64_t)pos * g.pstride);
     }
   } else {
-    const int tot = np * nvalid;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int l = i / np;
-      const int pos = i - l * np;
-      fn(l, pos, lb[l] + pos);
-    }
+    for (int l = 0; l < nvalid; ++l)
+      for (int pos = threadIdx.x; pos < np; pos += blockDim.x) fn(l, pos, lb[l] + pos);
   }
 }
 
-// Scaled first derivative e at (line, pos): phi at junctions and ends, the solve elsewhere.
-template <typename T, class BUN>
-__device__ __forceinline__ T e_at(const T* O, const double* phi, const BUN& bun, int p1, int M, int l, int pos) {
-  const int j = pos / M;
-  return (pos - j * M == 0) ? (T)phi[l * p1 + j] : O[bun.at(l, pos)];
+__device__ __forceinline__ int log2_pow2(int L) { return __ffs(L) - 1; }
+
+// Four consecutive elements starting at a 16-byte aligned address.
+__device__ __forceinline__ void ld4(const float* p, float (&r)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  r[0] = t.x, r[1] = t.y, r[2] = t.z, r[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&r)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  r[0] = a.x, r[1] = a.y, r[2] = b.x, r[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&r)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&r)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(r[2], r[3]);
 }
 
 }  // namespace
@@ -126,25 +152,30 @@ __device__ __forceinline__ T e_at(const T* O, const double* phi, const BUN& bun,
 // ---------------------------------------------------------------------------------------------------------------
 // Stand-alone derivative d1 (and d2) along one axis; optional phi output.
 template <typename T, int LOGC, bool SFLAV>
-__global__ void __launch_bounds__(1024) k_deriv(DerivArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_deriv(DerivArgs<T> a) {
   constexpr int C = 1 << LOGC;
   extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, C> cc;
   const LineGeom& g = a.g;
   const bool want_d2 = a.d2 != nullptr;
-  Carve<T> cv(sm, g, want_d2 ? 3 : 2);
+  Carve<T> cv(sm, g, want_d2 ? 3 : 2, 0);
   T* F = cv.buf[0];
   T* O = cv.buf[1];
   T* O2 = cv.buf[2];
   const Bundle<LOGC, SFLAV> bun{g.pitch};
   const WorkMap<SFLAV> wm{g.L, g.p, g.NC};
+  const int logL = log2_pow2(g.L);
   const int nvalid = bundle_bases<SFLAV>(g, blockIdx.x, cv.lb);
+  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
   __syncthreads();
-  load_lines<T, SFLAV>(a.f, F, bun, g, cv.lb, nvalid);
+  stage_padded<T, SFLAV>(a.f, F, bun, g, cv.lb, nvalid, logL);
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
-  pmbc_phi<T, 8>(F, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+  pmbc_phi<T, 16>(F, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
   __syncthreads();
+  const int p1 = g.p + 1;
   if (a.phi_out) {
-    const int p1 = g.p + 1;
     for (int i = threadIdx.x; i < nvalid * p1; i += blockDim.x) {
       const int l = i / p1;
       int64_t line;
@@ -158,32 +189,30 @@ __global__ void __launch_bounds__(1024) k_deriv(DerivArgs<T> a) {
     }
   }
   if (a.d1 == nullptr) return;
-  solve_bundle<T, C, SFLAV>(F, O, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
-                            BndPhi<T>{cv.phi, g.p + 1});
-  const int p1 = g.p + 1;
-  for_points<SFLAV>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
-    a.d1[gi] = a.s1 * e_at(O, cv.phi, bun, p1, g.M, l, pos);
+  solve_bundle<T, C, SFLAV>(F, O, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+                            BndPhi<T>{cv.phi, p1});
+  for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+    a.d1[gi] = a.s1 * O[bun.at(l, pos)];
   });
   if (!want_d2) return;
-  solve_bundle<T, C, SFLAV>(F, O2, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD2{},
+  solve_bundle<T, C, SFLAV>(F, O2, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD2{},
                             BndD2<T, Bundle<LOGC, SFLAV>>{F, O, cv.phi, p1, g.M, bun});
   // Output: interior slots from the solve; at a junction the average of the two patches' end values
   // (d2 h^2/6)_avg = (f_{j-1} - 2 f_j + f_{j+1} + e_{j-1} - e_{j+1}) / 2; at the two line ends the single value.
-  for_points<SFLAV>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
-    const int j = pos / g.M;
+  for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+    const int j = div_magic(pos, g.mmagic);
     T s;
-    if (pos - j * g.M != 0) {
+    if (pos != j * g.M) {
       s = O2[bun.at(l, pos)];
     } else {
       const T ej = (T)cv.phi[l * p1 + j];
       if (pos == 0) {
-        s = (F[bun.at(l, 1)] - F[bun.at(l, 0)]) - T(2) * ej - e_at(O, cv.phi, bun, p1, g.M, l, 1);
+        s = (F[bun.at(l, 1)] - F[bun.at(l, 0)]) - T(2) * ej - O[bun.at(l, 1)];
       } else if (pos == g.n) {
-        s = (F[bun.at(l, pos - 1)] - F[bun.at(l, pos)]) + T(2) * ej + e_at(O, cv.phi, bun, p1, g.M, l, pos - 1);
+        s = (F[bun.at(l, pos - 1)] - F[bun.at(l, pos)]) + T(2) * ej + O[bun.at(l, pos - 1)];
       } else {
         const T fm = F[bun.at(l, pos - 1)], f0 = F[bun.at(l, pos)], fp = F[bun.at(l, pos + 1)];
-        s = T(0.5) * (((fm - f0) + (fp - f0)) + (e_at(O, cv.phi, bun, p1, g.M, l, pos - 1) -
-                                                 e_at(O, cv.phi, bun, p1, g.M, l, pos + 1)));
+        s = T(0.5) * (((fm - f0) + (fp - f0)) + (O[bun.at(l, pos - 1)] - O[bun.at(l, pos + 1)]));
       }
     }
     a.d2[gi] = a.s2 * s;
@@ -193,122 +222,288 @@ __global__ void __launch_bounds__(1024) k_deriv(DerivArgs<T> a) {
 // ---------------------------------------------------------------------------------------------------------------
 // X kernel of the 2-D acoustic step: sub-step B on whole x lines, then the x part of sub-step A.
 template <typename T, int LOGC, bool KAHAN>
-__global__ void __launch_bounds__(1024) k_ac_x(AcXArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T> a) {
   constexpr int C = 1 << LOGC;
   extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, C> cc;
   const LineGeom& g = a.g;
-  Carve<T> cv(sm, g, 3);
+  Carve<T> cv(sm, g, 3, 4);
   T* V = cv.buf[0];  // v1 (old)
-  T* D = cv.buf[1];  // sigma after B
+  T* D = cv.buf[1];  // sigma, then sigma after B
   T* O = cv.buf[2];  // solve output
+  T* SK = cv.stg[0];  // kappa
+  T* ST = cv.stg[1];  // d_z v3
+  T* SC = cv.stg[2];  // compensation of sigma
+  T* SV = cv.stg[3];  // compensation of v1
   const Bundle<LOGC, false> bun{g.pitch};
   const WorkMap<false> wm{g.L, g.p, g.NC};
   const int nvalid = bundle_bases<false>(g, blockIdx.x, cv.lb);
   const int p1 = g.p + 1;
+  const int sp = g.spitch;
+  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
   __syncthreads();
-  load_lines<T, false>(a.v1, V, bun, g, cv.lb, nvalid);
-  if (!a.do_B) load_lines<T, false>(a.sigma, D, bun, g, cv.lb, nvalid);
-  __syncthreads();
+  stage_padded<T, false>(a.v1, V, bun, g, cv.lb, nvalid, 0);
+  stage_padded<T, false>(a.sigma, D, bun, g, cv.lb, nvalid, 0);
+  cp_async_commit();
   if (a.do_B) {
-    pmbc_phi<T, 8>(V, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+    stage_rows<T>(a.kappa, SK, g, cv.lb, nvalid);
+    stage_rows<T>(a.tmp, ST, g, cv.lb, nvalid);
+    if constexpr (KAHAN) stage_rows<T>(a.csig, SC, g, cv.lb, nvalid);
+  }
+  if constexpr (KAHAN) stage_rows<T>(a.cv1, SV, g, cv.lb, nvalid);
+  cp_async_commit();
+  if (a.do_B) {
+    cp_async_wait<1>();
     __syncthreads();
-    solve_bundle<T, C, false>(V, O, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+    pmbc_phi<T, 16>(V, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+    __syncthreads();
+    solve_bundle<T, C, false>(V, O, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
                               BndPhi<T>{cv.phi, p1});
+    cp_async_wait<0>();
+    __syncthreads();
     const int64_t r0 = (int64_t)blockIdx.x * g.L;
-    for_points<false>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
+    const int np = g.n + 1;
+    for (int l = 0; l < nvalid; ++l) {
       const int z = (int)((r0 + l) / g.ny1);
-      const T gx = a.s3h * e_at(O, cv.phi, bun, p1, g.M, l, pos);  // d_x v1
-      const T gz = a.tmp[gi];                                        // d_z v3
-      T inc;
-      if (a.pml && (a.xB.in(pos) || a.zB.in(z))) {
-        inc = a.xB.in(pos) ? a.xB.step(a.phix, gi, pos, gx) : -a.dt * gx;
-        inc += a.zB.in(z) ? a.zB.step(a.phiz, gi, z, gz) : -a.dt * gz;
-      } else {
-        inc = -a.dt * (gx + gz);
+      const bool zlay = a.pml && a.zB.in(z);
+      const bool srow = a.src.on && (unsigned)(z - a.src.zs + 12) < 25u;
+      const int64_t rb = cv.lb[l];
+      const T* stl = ST + l * sp;
+      const T* skl = SK + l * sp;
+      const T* scl = SC + l * sp;
+      // scalar update of one point (PML layers, source block, line tail)
+      auto one = [&](int pos) {
+        const int64_t gi = rb + pos;
+        const T gx = a.s3h * O[bun.at(l, pos)];  // d_x v1
+        const T gz = stl[pos];                   // d_z v3
+        T inc = (a.pml && a.xB.in(pos)) ? a.xB.step(a.phix, gi, pos, gx) : -a.dt * gx;
+        inc += zlay ? a.zB.step(a.phiz, gi, z, gz) : -a.dt * gz;
+        T delta = skl[pos] * inc;
+        if (srow) {
+          const int dx = pos - a.src.xs + 12;
+          if ((unsigned)dx < 25u) delta += (T)(a.src.amp * a.src.g[z - a.src.zs + 12] * a.src.g[dx]);
+        }
+        const int k = bun.at(l, pos);
+        T sg = D[k];
+        if constexpr (KAHAN) {
+          float c = scl[pos];
+          kahan_add(sg, c, delta);
+          a.csig[gi] = c;
+        } else {
+          sg += delta;
+        }
+        a.sigma[gi] = sg;
+        D[k] = sg;
+      };
+      // four points per thread, lanes on consecutive positions (conflict-free on the padded buffers)
+      const int T4 = 4 * blockDim.x;
+      for (int q0 = threadIdx.x; q0 < np; q0 += T4) {
+        T gz[4], kp[4], cc[4], ox[4], sg[4];
+        bool fastp[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = q0 + t * blockDim.x;
+          fastp[t] = pos < np && !zlay && !(a.pml && a.xB.in(pos)) && !(srow && (unsigned)(pos - a.src.xs + 12) < 25u);
+          if (fastp[t]) {
+            const int k = bun.at(l, pos);
+            gz[t] = stl[pos];
+            kp[t] = skl[pos];
+            if constexpr (KAHAN) cc[t] = scl[pos];
+            ox[t] = O[k];
+            sg[t] = D[k];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = q0 + t * blockDim.x;
+          if (!fastp[t]) {
+            if (pos < np) one(pos);
+            continue;
+          }
+          const T delta = kp[t] * (-a.dt * (a.s3h * ox[t] + gz[t]));
+          if constexpr (KAHAN) {
+            kahan_add(sg[t], cc[t], delta);
+            a.csig[rb + pos] = cc[t];
+          } else {
+            sg[t] += delta;
+          }
+          a.sigma[rb + pos] = sg[t];
+          D[bun.at(l, pos)] = sg[t];
+        }
       }
-      T delta = a.kappa[gi] * inc;
-      if (a.src.on) {
-        const int dz = z - a.src.zs + 12, dx = pos - a.src.xs + 12;
-        if ((unsigned)dz < 25u && (unsigned)dx < 25u) delta += (T)(a.src.amp * a.src.g[dz] * a.src.g[dx]);
-      }
-      T s = a.sigma[gi];
-      if constexpr (KAHAN) {
-        float c = a.csig[gi];
-        kahan_add(s, c, delta);
-        a.csig[gi] = c;
-      } else {
-        s += delta;
-      }
-      a.sigma[gi] = s;
-      D[bun.at(l, pos)] = s;
-    });
+    }
+    __syncthreads();
+  } else {
+    cp_async_wait<0>();
     __syncthreads();
   }
-  pmbc_phi<T, 8>(D, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+  pmbc_phi<T, 16>(D, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
   __syncthreads();
-  solve_bundle<T, C, false>(D, O, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+  solve_bundle<T, C, false>(D, O, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
                             BndPhi<T>{cv.phi, p1});
-  for_points<false>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
-    const T gx = a.s3h * e_at(O, cv.phi, bun, p1, g.M, l, pos);  // d_x sigma
-    const T inc = (a.pml && a.xA.in(pos)) ? a.xA.step(a.psix, gi, pos, gx) : -a.acoef * gx;
-    const T delta = a.b[gi] * inc;
-    T v = V[bun.at(l, pos)];
-    if constexpr (KAHAN) {
-      float c = a.cv1[gi];
-      kahan_add(v, c, delta);
-      a.cv1[gi] = c;
-    } else {
-      v += delta;
+  {
+    const int np = g.n + 1;
+    for (int l = 0; l < nvalid; ++l) {
+      const int64_t rb = cv.lb[l];
+      const T* svl = SV + l * sp;
+      auto one = [&](int pos) {
+        const int64_t gi = rb + pos;
+        const T gx = a.s3h * O[bun.at(l, pos)];  // d_x sigma
+        const T inc = (a.pml && a.xA.in(pos)) ? a.xA.step(a.psix, gi, pos, gx) : -a.acoef * gx;
+        const T delta = (a.b ? a.b[gi] : a.b0) * inc;
+        T v = V[bun.at(l, pos)];
+        if constexpr (KAHAN) {
+          float c = svl[pos];
+          kahan_add(v, c, delta);
+          a.cv1[gi] = c;
+        } else {
+          v += delta;
+        }
+        a.v1[gi] = v;
+      };
+      const int T4 = 4 * blockDim.x;
+      const T sc = -a.acoef * a.b0 * a.s3h;
+      for (int q0 = threadIdx.x; q0 < np; q0 += T4) {
+        T ox[4], vv[4], cc[4];
+        bool fastp[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = q0 + t * blockDim.x;
+          fastp[t] = pos < np && !a.b && !(a.pml && a.xA.in(pos));
+          if (fastp[t]) {
+            const int k = bun.at(l, pos);
+            ox[t] = O[k];
+            vv[t] = V[k];
+            if constexpr (KAHAN) cc[t] = svl[pos];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pos = q0 + t * blockDim.x;
+          if (!fastp[t]) {
+            if (pos < np) one(pos);
+            continue;
+          }
+          const T delta = sc * ox[t];
+          if constexpr (KAHAN) {
+            kahan_add(vv[t], cc[t], delta);
+            a.cv1[rb + pos] = cc[t];
+          } else {
+            vv[t] += delta;
+          }
+          a.v1[rb + pos] = vv[t];
+        }
+      }
     }
-    a.v1[gi] = v;
-  });
+  }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
 // Z kernel of the 2-D acoustic step: z part of sub-step A on whole z lines, then tmp = d_z v3.
 template <typename T, int LOGC, bool KAHAN>
-__global__ void __launch_bounds__(1024) k_ac_z(AcZArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T> a) {
   constexpr int C = 1 << LOGC;
   extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, C> cc;
   const LineGeom& g = a.g;
-  Carve<T> cv(sm, g, 2);
+  Carve<T> cv(sm, g, 2, 0);
   T* S = cv.buf[0];  // sigma, then v3 (new)
   T* O = cv.buf[1];
   const Bundle<LOGC, true> bun{g.pitch};
   const WorkMap<true> wm{g.L, g.p, g.NC};
+  const int logL = log2_pow2(g.L);
   const int nvalid = bundle_bases<true>(g, blockIdx.x, cv.lb);
+  const int np = g.n + 1;
   const int p1 = g.p + 1;
+  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
   __syncthreads();
-  load_lines<T, true>(a.sigma, S, bun, g, cv.lb, nvalid);
+  {
+    // L2 prefetch of the bundle's segments of every array read later (segments of L elements start on
+    // L * sizeof(T)-byte boundaries of the padded layout).
+    const T* arrs[3] = {a.v3, a.b, a.cv3};
+    const uint32_t sb = (uint32_t)(g.L * sizeof(T));
+    if ((sb & 15u) == 0)
+      for (int i = threadIdx.x; i < 3 * np; i += blockDim.x) {
+        const T* base = arrs[i / np];
+        if (base) prefetch_l2(base + cv.lb[0] + (int64_t)(i % np) * g.pstride, sb);
+      }
+  }
+  stage_padded<T, true>(a.sigma, S, bun, g, cv.lb, nvalid, logL);
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
-  pmbc_phi<T, 8>(S, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+  pmbc_phi<T, 16>(S, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
   __syncthreads();
-  solve_bundle<T, C, true>(S, O, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+  solve_bundle<T, C, true>(S, O, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
                            BndPhi<T>{cv.phi, p1});
-  for_points<true>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
-    const T gz = a.s3h * e_at(O, cv.phi, bun, p1, g.M, l, pos);  // d_z sigma
+  // update of v3; lines are handled in groups of four neighbouring x (16-byte vectors) where possible
+  const int lg = g.L >= 4 ? logL - 2 : 0;   // log2 of the number of 4-line groups per position
+  const int wl = g.L >= 4 ? 4 : g.L;        // lines per item
+  auto one = [&](int l, int pos) {
+    const int64_t gi = cv.lb[l] + (int64_t)pos * g.pstride;
+    const T gz = a.s3h * O[bun.at(l, pos)];  // d_z sigma
     const T inc = (a.pml && a.zA.in(pos)) ? a.zA.step(a.psiz, gi, pos, gz) : -a.acoef * gz;
-    const T delta = a.b[gi] * inc;
-    T v = a.v3[gi];
+    const T delta = (a.b ? a.b[gi] : a.b0) * inc;
+    T vv = a.v3[gi];
     if constexpr (KAHAN) {
-      float c = a.cv3[gi];
-      kahan_add(v, c, delta);
-      a.cv3[gi] = c;
+      float cc = a.cv3[gi];
+      kahan_add(vv, cc, delta);
+      a.cv3[gi] = cc;
     } else {
-      v += delta;
+      vv += delta;
     }
-    a.v3[gi] = v;
-    S[bun.at(l, pos)] = v;
-  });
+    a.v3[gi] = vv;
+    S[bun.at(l, pos)] = vv;
+  };
+  const int items = np << lg;
+  const T sc = -a.acoef * a.b0 * a.s3h;
+  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    const int pos = i >> lg;
+    const int l0 = (i & ((1 << lg) - 1)) * wl;
+    if (g.L < 4 || l0 + 3 >= nvalid || a.b || (a.pml && a.zA.in(pos))) {
+      for (int t = 0; t < wl; ++t)
+        if (l0 + t < nvalid) one(l0 + t, pos);
+      continue;
+    }
+    const int64_t gi = cv.lb[l0] + (int64_t)pos * g.pstride;
+    const int k = bun.at(l0, pos);
+    T v[4], c[4], o[4];
+    ld4(a.v3 + gi, v);
+    if constexpr (KAHAN) ld4(a.cv3 + gi, c);
+    ld4(O + k, o);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const T delta = sc * o[t];
+      if constexpr (KAHAN) {
+        kahan_add(v[t], c[t], delta);
+      } else {
+        v[t] += delta;
+      }
+    }
+    st4(a.v3 + gi, v);
+    if constexpr (KAHAN) st4(a.cv3 + gi, c);
+    st4(S + k, v);
+  }
   __syncthreads();
   if (!a.do_tmp) return;
-  pmbc_phi<T, 8>(S, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+  pmbc_phi<T, 16>(S, bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
   __syncthreads();
-  solve_bundle<T, C, true>(S, O, cv.sA, cv.sB, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+  solve_bundle<T, C, true>(S, O, cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
                            BndPhi<T>{cv.phi, p1});
-  for_points<true>(g, cv.lb, nvalid, [&](int l, int pos, int64_t gi) {
-    a.tmp[gi] = a.s3h * e_at(O, cv.phi, bun, p1, g.M, l, pos);
-  });
+  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    const int pos = i >> lg;
+    const int l0 = (i & ((1 << lg) - 1)) * wl;
+    if (g.L < 4 || l0 + 3 >= nvalid) {
+      for (int t = 0; t < wl; ++t)
+        if (l0 + t < nvalid) a.tmp[cv.lb[l0 + t] + (int64_t)pos * g.pstride] = a.s3h * O[bun.at(l0 + t, pos)];
+      continue;
+    }
+    T o[4];
+    ld4(O + bun.at(l0, pos), o);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) o[t] *= a.s3h;
+    st4(a.tmp + cv.lb[l0] + (int64_t)pos * g.pstride, o);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -325,9 +520,11 @@ __global__ void k_gather(const T* __restrict__ f, const int64_t* __restrict__ id
 
 // ---------------------------------------------------------------------------------------------------------------
 // Host launchers.
-size_t smem_bytes(const LineGeom& g, int nbuf, size_t esize) {
+size_t smem_bytes(const LineGeom& g, int nbuf, int nstage, size_t esize) {
   const size_t nw = (size_t)g.L * g.p * g.NC;
   size_t b = (size_t)nbuf * g.buf * esize;
+  b = (b + 15) & ~size_t(15);
+  b += (size_t)nstage * g.stage * esize;
   b = (b + 15) & ~size_t(15);
   b += 2 * nw * esize;
   b = (b + 15) & ~size_t(15);
@@ -347,30 +544,30 @@ static cudaError_t launch(K kern, int grid, int threads, size_t smem, cudaStream
 
 template <typename T>
 cudaError_t launch_deriv(const DerivArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.g, a.d2 ? 3 : 2, sizeof(T));
+  const size_t smem = smem_bytes(a.g, a.d2 ? 3 : 2, 0, sizeof(T));
   DerivArgs<T> args = a;
   if (sflav) {
-    if (logc == 4) return launch(k_deriv<T, 4, true>, a.g.nbundles, threads, smem, st, &args);
-    return launch(k_deriv<T, 5, true>, a.g.nbundles, threads, smem, st, &args);
+    if (logc == 3 && sizeof(T) == 4) return launch(k_deriv<T, 3, true>, a.g.nbundles, threads, smem, st, &args);
+    return launch(k_deriv<T, 4, true>, a.g.nbundles, threads, smem, st, &args);
   }
-  if (logc == 4) return launch(k_deriv<T, 4, false>, a.g.nbundles, threads, smem, st, &args);
-  return launch(k_deriv<T, 5, false>, a.g.nbundles, threads, smem, st, &args);
+  if (logc == 3 && sizeof(T) == 4) return launch(k_deriv<T, 3, false>, a.g.nbundles, threads, smem, st, &args);
+  return launch(k_deriv<T, 4, false>, a.g.nbundles, threads, smem, st, &args);
 }
 
 template <typename T, bool KAHAN>
 cudaError_t launch_ac_x(const AcXArgs<T>& a, int logc, int threads, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.g, 3, sizeof(T));
+  const size_t smem = smem_bytes(a.g, 3, 4, sizeof(T));
   AcXArgs<T> args = a;
-  if (logc == 4) return launch(k_ac_x<T, 4, KAHAN>, a.g.nbundles, threads, smem, st, &args);
-  return launch(k_ac_x<T, 5, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+  if (logc == 3 && sizeof(T) == 4) return launch(k_ac_x<T, 3, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+  return launch(k_ac_x<T, 4, KAHAN>, a.g.nbundles, threads, smem, st, &args);
 }
 
 template <typename T, bool KAHAN>
 cudaError_t launch_ac_z(const AcZArgs<T>& a, int logc, int threads, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.g, 2, sizeof(T));
+  const size_t smem = smem_bytes(a.g, 2, 0, sizeof(T));
   AcZArgs<T> args = a;
-  if (logc == 4) return launch(k_ac_z<T, 4, KAHAN>, a.g.nbundles, threads, smem, st, &args);
-  return launch(k_ac_z<T, 5, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+  if (logc == 3 && sizeof(T) == 4) return launch(k_ac_z<T, 3, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+  return launch(k_ac_z<T, 4, KAHAN>, a.g.nbundles, threads, smem, st, &args);
 }
 
 template <typename T>

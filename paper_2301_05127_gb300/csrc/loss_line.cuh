@@ -44,6 +44,9 @@ struct Bundle {
   __device__ __forceinline__ int at(int line, int pos) const {
     return SFLAV ? padpos<LOGC>(pos) * pitch + line : line * pitch + padpos<LOGC>(pos);
   }
+  // Offset of position s0 + r from position s0 when s0 is a multiple of 2^LOGC and 0 <= r < 2^(LOGC+1):
+  // compile-time for a compile-time r (X flavour) or one multiply (S flavour).
+  __device__ __forceinline__ int rel(int r) const { return SFLAV ? (r + (r >> LOGC)) * pitch : r + (r >> LOGC); }
 };
 
 // Work item w <-> (line, patch, chunk).
@@ -97,10 +100,16 @@ __device__ void pmbc_phi(const T* __restrict__ f, const BUN& bun, int L, int nva
     const int c = j * M;
     const int mlo = max(-n_nb, -c);
     const int mhi = min(n_nb, n - c);
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;  // two independent accumulators shorten the FP64 dependency chain
     if (line < nvalid) {
       const double* wj = W + (size_t)j * wlen + n_nb;
-      for (int m = mlo + g; m <= mhi; m += G) s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
+      int m = mlo + g;
+      for (; m + G <= mhi; m += 2 * G) {
+        s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
+        s2 = fma(__ldg(wj + m + G), (double)f[bun.at(line, c + m + G)], s2);
+      }
+      if (m <= mhi) s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
+      s += s2;
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
@@ -119,114 +128,194 @@ struct RhsD2 {
   __device__ __forceinline__ T operator()(T fm1, T f0, T fp1) const { return (fp1 - f0) - (f0 - fm1); }
 };
 
-// Solve e_{i-1} + 4 e_i + e_{i+1} = q_i (i = 1..M-1) on every patch of every line of the bundle, with
-// Dirichlet values from bnd.left(line, patch) / bnd.right(line, patch).  Writes e_i (i = 1..M-1) into `out`
-// at the same (line, position) slots as f; junction slots of `out` are not written.  sA/sB hold two values
-// per work item.  Must be called by all threads of the block (contains __syncthreads).
-template <typename T, int C, bool SFLAV, class BUN, class RHS, class BND>
-__device__ void solve_bundle(const T* __restrict__ f, T* __restrict__ out, T* __restrict__ sA, T* __restrict__ sB,
-                             const BUN& bun, const WorkMap<SFLAV>& wm, int nvalid, int M, const float* t32,
-                             const double* t64, T minf, RHS rhs, BND bnd) {
-  const int nwork = wm.count();
-  // Pass 1: forward summaries with zero carry-in.
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    int line, patch, chunk;
-    wm.decode(w, line, patch, chunk);
-    T P = T(1), y = T(0);
-    if (line < nvalid) {
-      const int a = 1 + chunk * C;
-      const int len = min(C, M - a);
-      const int base = patch * M;
-      T fm1 = f[bun.at(line, base + a - 1)];
-      T f0 = f[bun.at(line, base + a)];
+// Per-block constants of the chunked solve, by chunk class (0: first chunk of a patch, which uses the exact
+// leading Thomas factors; 1: a full middle chunk; 2: the last chunk).  For a chunk of length len with local
+// forward sweep y_hat (zero carry-in) and local backward sweep e_hat (zero carry-out), the exact solution is
+//     y_j = y_hat_j + P_j y_in,        e_j = e_hat_j + alpha_j y_in + beta_j e_out,
+// where P_j = prod_{k<=j} (-m_fwd(k)), alpha is the backward sweep applied to P and beta_j = prod (-m_bwd(k)),
+// all independent of the data.  Pend = P_{len-1}, A = alpha_0, B = beta_0 summarise a chunk for the carries.
+template <typename T, int C>
+struct ChunkClasses {
+  T alpha[3][C + 1];  // stride C + 1: the three classes fall on different banks
+  T beta[3][C + 1];
+  T Pend[3], A[3], B[3];
+  int len[3];
+  T mt[kMaxTable];  // Thomas factors m_0..m_63 in the working precision
+};
+
+template <typename T, int C>
+__device__ void chunk_classes_init(ChunkClasses<T, C>* cc, int M, int NC, const float* t32, const double* t64,
+                                   T minf) {
+  for (int j = threadIdx.x; j < kMaxTable; j += blockDim.x) cc->mt[j] = Tab<T>::m(t32, t64, j);
+  const int cls = threadIdx.x;
+  if (cls < 3) {
+    int len;
+    if (cls == 0) len = min(C, M - 1);
+    else if (cls == 1) len = C;
+    else len = (M - 1) - (NC - 1) * C;
+    if (cls == 2 && NC == 1) len = min(C, M - 1);
+    cc->len[cls] = len;
+    T P[C];
+    T p = T(1);
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        if (j < len) {
-          const T fp1 = f[bun.at(line, base + a + j + 1)];
-          const T m = (chunk == 0) ? Tab<T>::m(t32, t64, j) : minf;  // m_{i-1}, i - 1 = chunk*C + j
-          y = rhs(fm1, f0, fp1) - m * y;
-          P = -m * P;
-          fm1 = f0;
-          f0 = fp1;
-        }
+    for (int j = 0; j < C; ++j) {
+      const T m = (cls == 0) ? Tab<T>::m(t32, t64, j) : minf;
+      p = -m * p;
+      P[j] = p;
+    }
+    T al = T(0), be = T(1);
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {
+      if (j < len) {
+        const T m = (cls == 0) ? Tab<T>::m(t32, t64, j + 1) : minf;
+        al = m * (P[j] - al);
+        be = -m * be;
       }
+      cc->alpha[cls][j] = al;
+      cc->beta[cls][j] = be;
     }
-    sA[w] = P;
-    sB[w] = y;
+    T pend = T(1);
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (j < len) pend = P[j];
+    cc->Pend[cls] = pend;
+    cc->A[cls] = al;
+    cc->B[cls] = be;
   }
-  __syncthreads();
-  // Pass 2: forward recurrence from the composed carry; y into out.
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    int line, patch, chunk;
-    wm.decode(w, line, patch, chunk);
-    if (line >= nvalid) continue;
-    T y = bnd.left(line, patch);
-    for (int k = 0; k < chunk; ++k) {
-      const int s = wm.sibling(w, chunk, k);
-      y = sB[s] + sA[s] * y;
-    }
-    const int a = 1 + chunk * C;
-    const int len = min(C, M - a);
-    const int base = patch * M;
-    T fm1 = f[bun.at(line, base + a - 1)];
-    T f0 = f[bun.at(line, base + a)];
+}
+
+// Solve e_{i-1} + 4 e_i + e_{i+1} = q_i (i = 1..M-1) on every patch of every line of the bundle, with
+// Dirichlet values e_0 = bnd.left(line, patch), e_M = bnd.right(line, patch).  Writes e_i for i = 1..M-1 into
+// `out` at the (line, position) slots of f, plus the left value at each patch start and the right value at
+// the last line end, so `out` holds e at every point of every line.  One work item (chunk) per thread
+// (wm.count() <= blockDim.x); sum holds 2 values per work item; cc from chunk_classes_init.  Must be called by
+// all threads of the block (contains __syncthreads).
+//
+// Carries: with y_in(0) = e_0 and y_in(k+1) = Y_k + Pend_k y_in(k) (forward), and
+// e_out(NC-1) = e_M, e_out(k-1) = E_k + A_k y_in(k) + B_k e_out(k) (backward), every chunk needs its own y_in
+// and e_out.  When the chunks of a (line, patch) are aligned groups of consecutive lanes (X flavour, NC a power
+// of two) both recurrences are affine scans done with warp shuffles; otherwise each thread walks the chunk
+// summaries in shared memory.
+template <typename T, int C, bool SFLAV, class BUN, class RHS, class BND>
+__device__ void solve_bundle(const T* __restrict__ f, T* __restrict__ out, T* __restrict__ sum,
+                             const ChunkClasses<T, C>* __restrict__ cc, const BUN& bun, const WorkMap<SFLAV>& wm,
+                             int nvalid, int M, const float* t32, const double* t64, T minf, RHS rhs, BND bnd) {
+  constexpr int LOGC = (C == 32) ? 5 : ((C == 16) ? 4 : 3);
+  static_assert((1 << LOGC) == C, "chunk length must be 8, 16 or 32");
+  const int nwork = wm.count();
+  const int w = threadIdx.x;
+  int line = 0, patch = 0, chunk = 0;
+  if (w < nwork) wm.decode(w, line, patch, chunk);
+  const bool act = w < nwork && line < nvalid;
+  const int NC = wm.NC;
+  const int cls = (chunk == 0) ? 0 : (chunk == NC - 1 ? 2 : 1);
+  const int len = act ? cc->len[cls] : 0;
+  const int s0 = patch * M + chunk * C;  // position of the left neighbour of the chunk's first unknown
+  const bool fast = (M & (C - 1)) == 0;  // chunk starts are multiples of C: compile-time offsets
+  T v[C];
+  T yend = T(0), ebeg = T(0);
+  if (act) {
+    const T* fp = f + bun.at(line, s0);
+    T fm1 = fast ? fp[bun.rel(0)] : f[bun.at(line, s0)];
+    T f0 = fast ? fp[bun.rel(1)] : f[bun.at(line, s0 + 1)];
+    T y = T(0);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       if (j < len) {
-        const T fp1 = f[bun.at(line, base + a + j + 1)];
-        const T m = (chunk == 0) ? Tab<T>::m(t32, t64, j) : minf;
+        const T fp1 = fast ? fp[bun.rel(j + 2)] : f[bun.at(line, s0 + j + 2)];
+        T m = minf;
+        if (chunk == 0) m = cc->mt[j];
         y = rhs(fm1, f0, fp1) - m * y;
-        out[bun.at(line, base + a + j)] = y;
+        v[j] = y;
         fm1 = f0;
         f0 = fp1;
       }
     }
-  }
-  __syncthreads();
-  // Pass 3: backward summaries with zero carry-in.
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    int line, patch, chunk;
-    wm.decode(w, line, patch, chunk);
-    T R = T(1), e = T(0);
-    if (line < nvalid) {
-      const int a = 1 + chunk * C;
-      const int len = min(C, M - a);
-      const int base = patch * M;
-#pragma unroll
-      for (int j = C - 1; j >= 0; --j) {
-        if (j < len) {
-          const T m = (chunk == 0) ? Tab<T>::m(t32, t64, j + 1) : minf;  // m_i, i = chunk*C + j + 1
-          e = m * (out[bun.at(line, base + a + j)] - e);
-          R = -m * R;
-        }
-      }
-    }
-    sA[w] = R;
-    sB[w] = e;
-  }
-  __syncthreads();
-  // Pass 4: backward recurrence from the composed carry; e into out (in place over y).
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    int line, patch, chunk;
-    wm.decode(w, line, patch, chunk);
-    if (line >= nvalid) continue;
-    T e = bnd.right(line, patch);
-    for (int k = wm.NC - 1; k > chunk; --k) {
-      const int s = wm.sibling(w, chunk, k);
-      e = sB[s] + sA[s] * e;
-    }
-    const int a = 1 + chunk * C;
-    const int len = min(C, M - a);
-    const int base = patch * M;
+    yend = y;
+    T e = T(0);
 #pragma unroll
     for (int j = C - 1; j >= 0; --j) {
       if (j < len) {
-        const T m = (chunk == 0) ? Tab<T>::m(t32, t64, j + 1) : minf;
-        const int k = bun.at(line, base + a + j);
-        e = m * (out[k] - e);
-        out[k] = e;
+        T m = minf;
+        if (chunk == 0) m = cc->mt[j + 1];
+        e = m * (v[j] - e);
+        v[j] = e;
       }
     }
+    ebeg = e;
+  }
+  T myin, eout;
+  const T left = act ? bnd.left(line, patch) : T(0);
+  const T right = act ? bnd.right(line, patch) : T(0);
+  const bool shfl = !SFLAV && NC <= 32 && (NC & (NC - 1)) == 0;
+  if (shfl) {
+    // forward inclusive scan of x -> Y + P x over the NC lanes of the group
+    const int g = w & (NC - 1);
+    T P = cc->Pend[cls], Y = yend;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      if (d >= NC) break;
+      const T Pp = __shfl_up_sync(0xffffffffu, P, d, NC);
+      const T Yp = __shfl_up_sync(0xffffffffu, Y, d, NC);
+      if (g >= d) {
+        Y = Y + P * Yp;
+        P = P * Pp;
+      }
+    }
+    const T yout = Y + P * left;  // y at the end of this chunk
+    const T yprev = __shfl_up_sync(0xffffffffu, yout, 1, NC);
+    myin = (g == 0) ? left : yprev;
+    // backward suffix scan of x -> K + B x, K = E + A y_in
+    T Bm = cc->B[cls], K = ebeg + cc->A[cls] * myin;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      if (d >= NC) break;
+      const T Bn = __shfl_down_sync(0xffffffffu, Bm, d, NC);
+      const T Kn = __shfl_down_sync(0xffffffffu, K, d, NC);
+      if (g + d < NC) {
+        K = K + Bm * Kn;
+        Bm = Bm * Bn;
+      }
+    }
+    const T ea = K + Bm * right;  // e at the start of this chunk
+    const T enext = __shfl_down_sync(0xffffffffu, ea, 1, NC);
+    eout = (g == NC - 1) ? right : enext;
+  } else {
+    if (act) {
+      sum[w] = yend;
+      sum[nwork + w] = ebeg;
+    }
+    __syncthreads();
+    T yin = left, acc = T(0), prod = T(1);
+    myin = left;
+    if (act) {
+      for (int k = 0; k < NC; ++k) {
+        const int ck = (k == 0) ? 0 : (k == NC - 1 ? 2 : 1);
+        const int sk = wm.sibling(w, chunk, k);
+        if (k == chunk) myin = yin;
+        if (k > chunk) {
+          acc += prod * (sum[nwork + sk] + cc->A[ck] * yin);
+          prod *= cc->B[ck];
+        }
+        yin = sum[sk] + cc->Pend[ck] * yin;
+      }
+    }
+    eout = acc + prod * right;
+  }
+  if (act) {
+    T* op = out + bun.at(line, s0);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      if (j < len) {
+        const T e = v[j] + cc->alpha[cls][j] * myin + cc->beta[cls][j] * eout;
+        if (fast)
+          op[bun.rel(j + 1)] = e;
+        else
+          out[bun.at(line, s0 + j + 1)] = e;
+      }
+    }
+    if (chunk == 0) out[bun.at(line, patch * M)] = left;
+    if (chunk == NC - 1 && patch == wm.p - 1) out[bun.at(line, patch * M + M)] = right;
   }
   __syncthreads();
 }
@@ -261,6 +350,30 @@ struct BndD2 {
     return (f[bun.at(line, b - 1)] - f[bun.at(line, b)]) + T(2) * eM + e[bun.at(line, b - 1)];
   }
 };
+
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async); no registers are used and the issuing
+// thread does not wait.  cp_async_wait<N>() waits until at most N committed groups are still in flight.
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// floor(pos / M) for 0 <= pos < 65536, 1 <= M < 32768, with magic = ceil(2^32 / M).
+__device__ __forceinline__ int div_magic(int pos, unsigned magic) { return (int)__umulhi((unsigned)pos, magic); }
+
+// Asynchronous bulk prefetch of [p, p + bytes) into L2 by the copy engine (bytes a multiple of 16, p 16-byte
+// aligned).  Issued at block start for every array a block will touch, so that DRAM streams while the block
+// solves; the later loads then hit L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Kahan-compensated u += delta (c carries the negated lost low-order part).
 __device__ __forceinline__ void kahan_add(float& u, float& c, float delta) {

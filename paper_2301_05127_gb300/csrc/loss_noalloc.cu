@@ -62,7 +62,7 @@ static loss_status_t noalloc_run(loss_ctx* h, Shot& s, int k, const T* f, T* d1,
   const int64_t sy = s.len[2], sz = s.len[2] * s.len[1];
   LineGeom g;
   int logc, threads;
-  loss_status_t st = line_geom(h, s, k, sz, sy, &g, &logc, &threads, 2);
+  loss_status_t st = line_geom(h, s, k, sz, sy, &g, &logc, &threads, 2, 0, 0, 0);
   if (st != LOSS_OK) return st;
   DerivArgs<T> a{};
   a.g = g;

@@ -31,14 +31,16 @@ template <typename T, bool K>
 static loss_status_t ac_x(loss_ctx* h, Shot& s, int do_B, double acoef, double src_amp) {
   LineGeom g;
   int logc, threads;
-  LOSS_TRY(line_geom(h, s, 2, s.sz, s.sy, &g, &logc, &threads, 3));
+  LOSS_TRY(line_geom(h, s, 2, s.sz, s.sy, &g, &logc, &threads, 3, 4, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_X],
+                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_X]));
   AcXArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[2], h->t32, h->t64};
   a.sigma = (T*)s.field[LOSS_FIELD_SIGMA];
   a.v1 = (T*)s.field[LOSS_FIELD_V1];
   a.kappa = (const T*)s.model[0];
-  a.b = (const T*)s.model[1];
+  a.b = s.b_const ? nullptr : (const T*)s.model[1];
+  a.b0 = (T)s.b0;
   a.tmp = (const T*)s.tmp[0];
   a.csig = (T*)s.comp[LOSS_FIELD_SIGMA];
   a.cv1 = (T*)s.comp[LOSS_FIELD_V1];
@@ -70,13 +72,15 @@ template <typename T, bool K>
 static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
   LineGeom g;
   int logc, threads;
-  LOSS_TRY(line_geom(h, s, 0, s.sz, s.sy, &g, &logc, &threads, 2));
+  LOSS_TRY(line_geom(h, s, 0, s.sz, s.sy, &g, &logc, &threads, 2, 0, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_Z],
+                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_Z]));
   AcZArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[0], h->t32, h->t64};
   a.sigma = (const T*)s.field[LOSS_FIELD_SIGMA];
   a.v3 = (T*)s.field[LOSS_FIELD_V3];
-  a.b = (const T*)s.model[1];
+  a.b = s.b_const ? nullptr : (const T*)s.model[1];
+  a.b0 = (T)s.b0;
   a.tmp = (T*)s.tmp[0];
   a.cv3 = (T*)s.comp[LOSS_FIELD_V3];
   a.acoef = (T)acoef;

@@ -18,7 +18,10 @@ struct LineGeom {
   int n_nb;    // PMBC halo width
   int L;       // lines per bundle
   int pitch;   // shared-memory pitch (X: per line, S: per position)
-  int buf;     // elements per shared-memory line buffer
+  int buf;     // elements per shared-memory line buffer (padded layout used by the solve)
+  int stage;   // elements per shared-memory staging buffer (dense rows of `spitch`, X flavour only)
+  int spitch;  // staging row pitch (n + 1 rounded up to 16 bytes)
+  unsigned mmagic;  // ceil(2^32 / M)
   int nbundles;
   // X flavour
   int ny1;
@@ -83,7 +86,8 @@ struct AcXArgs {
   T* sigma;
   T* v1;
   const T* kappa;
-  const T* b;        // buoyancy 1/rho
+  const T* b;        // buoyancy 1/rho, or null when constant (then b0)
+  T b0;
   const T* tmp;      // d_z v3 at the current half step (read when do_B)
   T* csig;           // Kahan compensation (KAHAN only)
   T* cv1;
@@ -106,7 +110,8 @@ struct AcZArgs {
   Tables tb;
   const T* sigma;
   T* v3;
-  const T* b;
+  const T* b;        // or null (then b0)
+  T b0;
   T* tmp;            // out: d_z v3 after the update (when do_tmp)
   T* cv3;
   T acoef;
