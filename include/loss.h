@@ -184,6 +184,9 @@ enum {
   LOSS_KERNEL_ACOUSTIC_Z = 1, /* 2-D acoustic: z part of the velocity sub-step and d_z v3 on z lines */
   LOSS_KERNEL_GATHER = 2,     /* receiver gather */
   LOSS_KERNEL_DERIVATIVE = 3, /* stand-alone derivative / phi (loss_derivative, loss_pmbc_phi) */
+  LOSS_KERNEL_ELASTIC_X = 4,  /* 3-D elastic passes on x lines */
+  LOSS_KERNEL_ELASTIC_Y = 5,  /* 3-D elastic passes on y lines */
+  LOSS_KERNEL_ELASTIC_Z = 6,  /* 3-D elastic passes on z lines */
   LOSS_NUM_KERNELS = 16
 };
 

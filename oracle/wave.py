@@ -214,23 +214,33 @@ _SIG = {(1, 1): "s11", (2, 2): "s22", (3, 3): "s33", (1, 2): "s12", (2, 1): "s12
         (3, 1): "s13", (2, 3): "s23", (3, 2): "s23"}
 
 
-def elastic_half_A(st, op, b, tau, src: Optional[Source], t):
+def _tau_deriv(op, f, comp, tau, pml: Optional[PML], mem, key):
+    """tau times the (PML-stretched) derivative of f along x_comp, integrated exactly over tau: tau d f outside
+    the layers, and -PML.advance(...) (the exact integral of (1/k) d f + Psi) inside."""
+    g = op.Dc(f, comp)
+    if pml is None:
+        return tau * g
+    return -pml.advance(mem[key], g, component_axis(comp, op.dim), tau)
+
+
+def elastic_half_A(st, op, b, tau, src: Optional[Source], t, pml: Optional[PML] = None, mem=None):
     """Subsystem A: v_i <- v_i + tau * b * (sum_j d_j sigma_ij + f_i)."""
     for i in (1, 2, 3):
-        acc = sum(op.Dc(st[_SIG[(i, j)]], j) for j in (1, 2, 3))
-        st[f"v{i}"] = st[f"v{i}"] + tau * b * acc
+        acc = sum(_tau_deriv(op, st[_SIG[(i, j)]], j, tau, pml, mem, f"psi_{i}{j}") for j in (1, 2, 3))
+        st[f"v{i}"] = st[f"v{i}"] + b * acc
     if src is not None and "force_z" in src.kinds:
         st["v3"][src.block] += tau * b[src.block] * ricker(t, src.f0, src.t0) * src.profile
 
 
-def elastic_B(st, op, lam, mu, dt, src: Optional[Source], t_half):
+def elastic_B(st, op, lam, mu, dt, src: Optional[Source], t_half, pml: Optional[PML] = None, mem=None):
     """Subsystem B: sigma_ij <- sigma_ij + dt * (lambda tr(e) delta_ij + 2 mu e_ij), e_ij = (d_j v_i + d_i v_j)/2."""
-    g = {(i, j): op.Dc(st[f"v{i}"], j) for i in (1, 2, 3) for j in (1, 2, 3)}  # g[i, j] = d_j v_i
-    tr = g[1, 1] + g[2, 2] + g[3, 3]
+    # x[i, j] = dt * d_j v_i (PML-stretched in the layers)
+    x = {(i, j): _tau_deriv(op, st[f"v{i}"], j, dt, pml, mem, f"phi_{i}{j}") for i in (1, 2, 3) for j in (1, 2, 3)}
+    tr = x[1, 1] + x[2, 2] + x[3, 3]
     for i in (1, 2, 3):
-        st[f"s{i}{i}"] = st[f"s{i}{i}"] + dt * (lam * tr + 2.0 * mu * g[i, i])
+        st[f"s{i}{i}"] = st[f"s{i}{i}"] + (lam * tr + 2.0 * mu * x[i, i])
     for (i, j) in ((1, 2), (1, 3), (2, 3)):
-        st[f"s{i}{j}"] = st[f"s{i}{j}"] + dt * mu * (g[i, j] + g[j, i])
+        st[f"s{i}{j}"] = st[f"s{i}{j}"] + mu * (x[i, j] + x[j, i])
     if src is not None:
         if "explosive" in src.kinds:
             for k in ("s11", "s22", "s33"):
@@ -239,10 +249,10 @@ def elastic_B(st, op, lam, mu, dt, src: Optional[Source], t_half):
             src.add(st["s13"], dt, t_half)
 
 
-def elastic_step(st, op, lam, mu, b, dt, t_n, src=None):
-    elastic_half_A(st, op, b, 0.5 * dt, src, t_n)
-    elastic_B(st, op, lam, mu, dt, src, t_n + 0.5 * dt)
-    elastic_half_A(st, op, b, 0.5 * dt, src, t_n + dt)
+def elastic_step(st, op, lam, mu, b, dt, t_n, src=None, pml=None, mem=None):
+    elastic_half_A(st, op, b, 0.5 * dt, src, t_n, pml, mem)
+    elastic_B(st, op, lam, mu, dt, src, t_n + 0.5 * dt, pml, mem)
+    elastic_half_A(st, op, b, 0.5 * dt, src, t_n + dt, pml, mem)
 
 
 def energy(st, physics, rho, moduli, h) -> float:
@@ -279,11 +289,13 @@ class Simulation:
         self.src = Source(w.src_index, w.src_kinds, w.f0, w.t0, w.amp, w.h, w.shape) if w.src_kinds else None
         self.pml, self.mem = None, None
         if getattr(w, "pml_width", 0) > 0:
-            if w.physics != "acoustic":
-                raise NotImplementedError("elastic PML")
             self.pml = PML(w.n, w.h, w.pml_width, w.pml_R, w.pml_kmax, w.f0, float(np.max(vp)))
-            comps = (1, 3) if w.dim == 2 else (1, 2, 3)
-            self.mem = {f"{k}{c}": np.zeros(w.shape) for k in ("psi", "phi") for c in comps}
+            if w.physics == "acoustic":
+                comps = (1, 3) if w.dim == 2 else (1, 2, 3)
+                self.mem = {f"{k}{c}": np.zeros(w.shape) for k in ("psi", "phi") for c in comps}
+            else:
+                self.mem = {f"{k}_{i}{j}": np.zeros(w.shape) for k in ("psi", "phi") for i in (1, 2, 3)
+                            for j in (1, 2, 3)}
         self.state = zero_state(w.physics, w.shape) if state is None else {k: np.array(v, dtype=np.float64) for k, v in state.items()}
         self.step_index = 0
         self.traces = {k: [] for k in w.receivers}
@@ -295,7 +307,7 @@ class Simulation:
             if w.physics == "acoustic":
                 acoustic_step(self.state, self.op, self.kappa, self.b, w.dt, t_n, self.src, self.pml, self.mem)
             else:
-                elastic_step(self.state, self.op, self.lam, self.mu, self.b, w.dt, t_n, self.src)
+                elastic_step(self.state, self.op, self.lam, self.mu, self.b, w.dt, t_n, self.src, self.pml, self.mem)
             self.step_index += 1
             if record:
                 for k, idx in w.receivers.items():

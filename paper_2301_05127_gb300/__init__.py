@@ -74,7 +74,8 @@ _PROTOS = {
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
-KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3}
+KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
+           "elastic_z": 6}
 
 
 def lib():

@@ -343,7 +343,8 @@ static loss_status_t setup_shot(loss_ctx* h, Shot& s) {
   }
   const int nmodel = d.physics == LOSS_ELASTIC ? 3 : 2;
   for (int m = 0; m < nmodel; ++m) LOSS_TRY(dev_zero_alloc(h, fb, &s.model[m]));
-  LOSS_TRY(dev_zero_alloc(h, fb, &s.tmp[0]));
+  const int ntmp = d.physics == LOSS_ELASTIC ? 8 : 1;
+  for (int i = 0; i < ntmp; ++i) LOSS_TRY(dev_zero_alloc(h, fb, &s.tmp[i]));
   // PMBC tables per used axis.
   for (int k = 0; k < 3; ++k) {
     if (s.dim == 2 && k == 1) continue;
@@ -570,6 +571,13 @@ loss_status_t loss_set_model(loss_handle_t h, int32_t shot, const double* vp, co
   s->b_const = true;
   for (int64_t i = 1; i < N && s->b_const; ++i) s->b_const = prho[i] == prho[0];
   s->b0 = 1.0 / prho[0];
+  if (el) {
+    s->lam_const = s->mu_const = true;
+    for (int64_t i = 1; i < N && s->lam_const; ++i) s->lam_const = md[0][i] == md[0][0];
+    for (int64_t i = 1; i < N && s->mu_const; ++i) s->mu_const = md[1][i] == md[1][0];
+    s->lam0 = md[0][0];
+    s->mu0 = md[1][0];
+  }
   for (int m = 0; m < nm; ++m) {
     if (s->esize == 8) {
       LOSS_TRY(copy_in(h, *s, s->model[m], md[m].data(), LOSS_MEM_HOST));
@@ -701,11 +709,17 @@ loss_status_t loss_set_pml(loss_handle_t h, int32_t shot, int32_t width, double 
                             "copy pml"));
       }
     }
+    if (s->d.physics == LOSS_ELASTIC) continue;
     if (!s->psi[k]) LOSS_TRY(dev_zero_alloc(h, fb, &s->psi[k]));
     if (!s->phi[k]) LOSS_TRY(dev_zero_alloc(h, fb, &s->phi[k]));
     LOSS_TRY(cuda_check(h, cudaMemsetAsync(s->psi[k], 0, fb, h->stream), "memset"));
     LOSS_TRY(cuda_check(h, cudaMemsetAsync(s->phi[k], 0, fb, h->stream), "memset"));
   }
+  if (s->d.physics == LOSS_ELASTIC)
+    for (int i = 0; i < 18; ++i) {
+      if (!s->pmem[i]) LOSS_TRY(dev_zero_alloc(h, fb, &s->pmem[i]));
+      LOSS_TRY(cuda_check(h, cudaMemsetAsync(s->pmem[i], 0, fb, h->stream), "memset"));
+    }
   return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
 }
 
@@ -826,6 +840,8 @@ loss_status_t loss_get_state(loss_handle_t h, void* blob, size_t* bytes) {
       if (field_used(s, f)) need += (size_t)s.dense * s.esize * (s.kahan ? 2 : 1);
     for (int k = 0; k < 3; ++k)
       if (s.psi[k]) need += 2 * (size_t)s.dense * s.esize;
+    for (int i = 0; i < 18; ++i)
+      if (s.pmem[i]) need += (size_t)s.dense * s.esize;
   }
   if (!blob) {
     *bytes = need;
@@ -855,6 +871,11 @@ loss_status_t loss_get_state(loss_handle_t h, void* blob, size_t* bytes) {
       LOSS_TRY(copy_out(h, s, p, s.psi[k], LOSS_MEM_HOST));
       p += (size_t)s.dense * s.esize;
       LOSS_TRY(copy_out(h, s, p, s.phi[k], LOSS_MEM_HOST));
+      p += (size_t)s.dense * s.esize;
+    }
+    for (int i = 0; i < 18; ++i) {
+      if (!s.pmem[i]) continue;
+      LOSS_TRY(copy_out(h, s, p, s.pmem[i], LOSS_MEM_HOST));
       p += (size_t)s.dense * s.esize;
     }
   }
@@ -892,6 +913,11 @@ loss_status_t loss_set_state(loss_handle_t h, const void* blob, size_t bytes) {
       LOSS_TRY(copy_in(h, s, s.psi[k], p, LOSS_MEM_HOST));
       p += (size_t)s.dense * s.esize;
       LOSS_TRY(copy_in(h, s, s.phi[k], p, LOSS_MEM_HOST));
+      p += (size_t)s.dense * s.esize;
+    }
+    for (int i = 0; i < 18; ++i) {
+      if (!s.pmem[i]) continue;
+      LOSS_TRY(copy_in(h, s, s.pmem[i], p, LOSS_MEM_HOST));
       p += (size_t)s.dense * s.esize;
     }
   }

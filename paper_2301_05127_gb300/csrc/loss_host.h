@@ -53,8 +53,12 @@ struct Shot {
   int pml_width = 0;
   double pml_R = 1e-6, pml_kmax = 1.0, pml_f0 = 0.0;
   void* pml_tab[3][3] = {};  // [axis slot][0: tau = dt, 1: dt/2, 2: -dt/2], each [4][n+1] in working precision
-  void* psi[3] = {};         // memory variables of the velocity sub-step, per derivative axis slot
-  void* phi[3] = {};         // memory variables of the stress sub-step
+  void* psi[3] = {};         // memory variables of the velocity sub-step, per derivative axis slot (acoustic)
+  void* phi[3] = {};         // memory variables of the stress sub-step (acoustic)
+  void* pmem[18] = {};       // elastic: 9 stress-sub-step terms d_j v_i at 3(i-1)+(j-1), then 9 velocity terms
+  void* rdelta[9] = {};      // receiver corrections of velocity term (i, j) at 3(i-1)+(j-1), layers only
+  bool lam_const = false, mu_const = false;
+  double lam0 = 0.0, mu0 = 0.0;
   // time stepping
   int64_t step = 0;
   bool staggered = false;  // velocities hold v at t_step + dt/2 instead of t_step
@@ -134,7 +138,10 @@ template <typename T, bool KAHAN>
 cudaError_t launch_ac_x(const AcXArgs<T>& a, int logc, int threads, cudaStream_t st);
 template <typename T, bool KAHAN>
 cudaError_t launch_ac_z(const AcZArgs<T>& a, int logc, int threads, cudaStream_t st);
+template <typename T, bool KAHAN>
+cudaError_t launch_el(const ElArgs<T>& a, int pass, int logc, int threads, cudaStream_t st);
 template <typename T>
-cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, cudaStream_t st);
+cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, const T* d0, const T* d1,
+                          const T* d2, cudaStream_t st);
 
 }  // namespace lossk

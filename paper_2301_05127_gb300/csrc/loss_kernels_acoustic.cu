@@ -18,136 +18,12 @@
 // pointwise updates, which arrive while the block solves.
 #include <cuda_runtime.h>
 
+#include "loss_block.cuh"
 #include "loss_line.cuh"
 #include "loss_types.h"
 
 namespace lossk {
 
-namespace {
-
-template <typename T>
-__device__ __forceinline__ T* align_ptr(void* p) {
-  uintptr_t u = reinterpret_cast<uintptr_t>(p);
-  u = (u + 15) & ~uintptr_t(15);
-  return reinterpret_cast<T*>(u);
-}
-
-// Shared-memory carve-up: nbuf padded line buffers, nstage dense staging buffers, two summary arrays, phi,
-// line bases.  Must match smem_bytes().
-template <typename T>
-struct Carve {
-  T* buf[3];
-  T* stg[4];
-  T* sA;
-  T* sB;
-  double* phi;
-  int64_t* lb;
-  __device__ Carve(unsigned char* sm, const LineGeom& g, int nbuf, int nstage) {
-    T* p = reinterpret_cast<T*>(sm);
-    for (int i = 0; i < 3; ++i) {
-      buf[i] = p;
-      if (i < nbuf) p += g.buf;
-    }
-    p = align_ptr<T>(p);
-    for (int i = 0; i < 4; ++i) {
-      stg[i] = p;
-      if (i < nstage) p += g.stage;
-    }
-    const int nw = g.L * g.p * g.NC;
-    sA = align_ptr<T>(p);
-    sB = sA + nw;
-    phi = align_ptr<double>(sB + nw);
-    lb = align_ptr<int64_t>(phi + g.L * (g.p + 1));
-  }
-};
-
-// Line bases of this block's bundle; returns the number of existing lines.
-template <bool SFLAV>
-__device__ __forceinline__ int bundle_bases(const LineGeom& g, int bundle, int64_t* lb) {
-  int nvalid;
-  if (SFLAV) {
-    const int outer = bundle / g.nxb;
-    const int x0 = (bundle - outer * g.nxb) * g.L;
-    nvalid = min(g.L, g.nx1 - x0);
-    for (int l = threadIdx.x; l < g.L; l += blockDim.x) lb[l] = (int64_t)outer * g.so + x0 + l;
-  } else {
-    const int64_t r0 = (int64_t)bundle * g.L;
-    nvalid = (int)min((int64_t)g.L, g.nrows - r0);
-    for (int l = threadIdx.x; l < g.L; l += blockDim.x) {
-      const int64_t r = r0 + l;
-      lb[l] = (r / g.ny1) * g.sz + (r % g.ny1) * g.sy;
-    }
-  }
-  return nvalid;
-}
-
-// Issue cp.async copies of whole lines of a global field into a padded line buffer (no wait).
-template <typename T, bool SFLAV, class BUN>
-__device__ __forceinline__ void stage_padded(const T* __restrict__ src, T* dst, const BUN& bun, const LineGeom& g,
-                                             const int64_t* lb, int nvalid, int logL) {
-  const int np = g.n + 1;
-  if (SFLAV) {
-    const int tot = np << logL;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int pos = i >> logL;
-      const int l = i & (g.L - 1);
-      if (l < nvalid) cp_async<sizeof(T)>(&dst[bun.at(l, pos)], src + lb[l] + (int64_t)pos * g.pstride);
-    }
-  } else {
-    for (int l = 0; l < nvalid; ++l)
-      for (int pos = threadIdx.x; pos < np; pos += blockDim.x)
-        cp_async<sizeof(T)>(&dst[bun.at(l, pos)], src + lb[l] + pos);
-  }
-}
-
-// Issue 16-byte cp.async copies of whole rows (X flavour) into a dense staging buffer of pitch g.spitch.
-template <typename T>
-__device__ __forceinline__ void stage_rows(const T* __restrict__ src, T* dst, const LineGeom& g, const int64_t* lb,
-                                           int nvalid) {
-  constexpr int V = 16 / sizeof(T);
-  const int nchunks = g.spitch / V;
-  for (int l = 0; l < nvalid; ++l)
-    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) cp_async<16>(dst + l * g.spitch + c * V, src + lb[l] + c * V);
-}
-
-
-// Iterate (line, pos, global offset) over the bundle in a coalesced order and call fn.
-template <bool SFLAV, class FN>
-__device__ __forceinline__ void for_points(const LineGeom& g, const int64_t* lb, int nvalid, int logL, FN fn) {
-  const int np = g.n + 1;
-  if (SFLAV) {
-    const int tot = np << logL;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int pos = i >> logL;
-      const int l = i & (g.L - 1);
-      if (l < nvalid) fn(l, pos, lb[l] + (int64_t)pos * g.pstride);
-    }
-  } else {
-    for (int l = 0; l < nvalid; ++l)
-      for (int pos = threadIdx.x; pos < np; pos += blockDim.x) fn(l, pos, lb[l] + pos);
-  }
-}
-
-__device__ __forceinline__ int log2_pow2(int L) { return __ffs(L) - 1; }
-
-// Four consecutive elements starting at a 16-byte aligned address.
-__device__ __forceinline__ void ld4(const float* p, float (&r)[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  r[0] = t.x, r[1] = t.y, r[2] = t.z, r[3] = t.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&r)[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-  r[0] = a.x, r[1] = a.y, r[2] = b.x, r[3] = b.y;
-}
-__device__ __forceinline__ void st4(float* p, const float (&r)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
-}
-__device__ __forceinline__ void st4(double* p, const double (&r)[4]) {
-  *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
-  *reinterpret_cast<double2*>(p + 2) = make_double2(r[2], r[3]);
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------------------------------------------
 // Stand-alone derivative d1 (and d2) along one axis; optional phi output.
@@ -349,8 +225,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T>
       auto one = [&](int pos) {
         const int64_t gi = rb + pos;
         const T gx = a.s3h * O[bun.at(l, pos)];  // d_x sigma
-        const T inc = (a.pml && a.xA.in(pos)) ? a.xA.step(a.psix, gi, pos, gx) : -a.acoef * gx;
-        const T delta = (a.b ? a.b[gi] : a.b0) * inc;
+        const T bb = a.b ? a.b[gi] : a.b0;
+        T inc;
+        if (a.pml && a.xA.in(pos)) {
+          const T ih = a.dlt ? a.xA.half(a.psix, gi, pos, gx) : T(0);
+          inc = a.xA.step(a.psix, gi, pos, gx);
+          if (a.dlt) a.dlt[gi] = bb * (ih - T(0.5) * inc);
+        } else {
+          inc = -a.acoef * gx;
+        }
+        const T delta = bb * inc;
         T v = V[bun.at(l, pos)];
         if constexpr (KAHAN) {
           float c = svl[pos];
@@ -442,8 +326,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T>
   auto one = [&](int l, int pos) {
     const int64_t gi = cv.lb[l] + (int64_t)pos * g.pstride;
     const T gz = a.s3h * O[bun.at(l, pos)];  // d_z sigma
-    const T inc = (a.pml && a.zA.in(pos)) ? a.zA.step(a.psiz, gi, pos, gz) : -a.acoef * gz;
-    const T delta = (a.b ? a.b[gi] : a.b0) * inc;
+    const T bb = a.b ? a.b[gi] : a.b0;
+    T inc;
+    if (a.pml && a.zA.in(pos)) {
+      const T ih = a.dlt ? a.zA.half(a.psiz, gi, pos, gz) : T(0);
+      inc = a.zA.step(a.psiz, gi, pos, gz);
+      if (a.dlt) a.dlt[gi] = bb * (ih - T(0.5) * inc);
+    } else {
+      inc = -a.acoef * gz;
+    }
+    const T delta = bb * inc;
     T vv = a.v3[gi];
     if constexpr (KAHAN) {
       float cc = a.cv3[gi];
@@ -509,12 +401,24 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T>
 // ---------------------------------------------------------------------------------------------------------------
 // Receiver gather: mode 0 out[r] = f[idx[r]]; mode 1 out[r] = (out[r] + f[idx[r]]) / 2 (integer-time velocity
 // from the two staggered half-step values).
+// Receiver gather.  mode 0: out[r] = f[idx[r]].  mode 1 (velocities, staggered state): out holds v_{n+1/2} and
+// f holds v_{n+3/2}; the integer-time value is v_{n+1/2} + (v_{n+3/2} - v_{n+1/2}) / 2 plus, inside absorbing
+// layers where the exponential sub-flow is not linear in the step length, the corrections d0..d2 (may be null).
 template <typename T>
 __global__ void k_gather(const T* __restrict__ f, const int64_t* __restrict__ idx, int64_t n, T* __restrict__ out,
-                         int mode) {
+                         int mode, const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const T v = f[idx[r]];
-    out[r] = mode ? T(0.5) * (out[r] + v) : v;
+    const int64_t q = idx[r];
+    const T v = f[q];
+    if (mode == 0) {
+      out[r] = v;
+    } else {
+      T c = T(0);
+      if (d0) c += d0[q];
+      if (d1) c += d1[q];
+      if (d2) c += d2[q];
+      out[r] = out[r] + T(0.5) * (v - out[r]) + c;
+    }
   }
 }
 
@@ -571,11 +475,12 @@ cudaError_t launch_ac_z(const AcZArgs<T>& a, int logc, int threads, cudaStream_t
 }
 
 template <typename T>
-cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, cudaStream_t st) {
+cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, const T* d0, const T* d1,
+                          const T* d2, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int threads = 256;
   const int grid = (int)((n + threads - 1) / threads < 4096 ? (n + threads - 1) / threads : 4096);
-  k_gather<T><<<grid, threads, 0, st>>>(f, idx, n, out, mode);
+  k_gather<T><<<grid, threads, 0, st>>>(f, idx, n, out, mode, d0, d1, d2);
   return cudaGetLastError();
 }
 
@@ -587,7 +492,9 @@ template cudaError_t launch_ac_x<double, false>(const AcXArgs<double>&, int, int
 template cudaError_t launch_ac_z<float, false>(const AcZArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_ac_z<float, true>(const AcZArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_ac_z<double, false>(const AcZArgs<double>&, int, int, cudaStream_t);
-template cudaError_t launch_gather<float>(const float*, const int64_t*, int64_t, float*, int, cudaStream_t);
-template cudaError_t launch_gather<double>(const double*, const int64_t*, int64_t, double*, int, cudaStream_t);
+template cudaError_t launch_gather<float>(const float*, const int64_t*, int64_t, float*, int, const float*,
+                                          const float*, const float*, cudaStream_t);
+template cudaError_t launch_gather<double>(const double*, const int64_t*, int64_t, double*, int, const double*,
+                                           const double*, const double*, cudaStream_t);
 
 }  // namespace lossk

@@ -1,0 +1,209 @@
+// sm_103a kernels of the 3-D elastic LOSS step (paper Sec. 2 velocity-stress system, Sec. 3.3 Strang
+// splitting with the exponential ADE-PML sub-flows).
+//
+// With the velocities half a step ahead (staggered state), one step is five line passes, each of which holds
+// whole lines of three fields along one axis on chip, closes them with the PMBC and solves them:
+//   BX (x lines):  TA = X[v1,x], TB = X[v2,x], TC = X[v3,x]
+//   BY (y lines):  TD = X[v2,y], TB += X[v1,y], TE = X[v3,y]
+//   BZ (z lines):  sigma_ii += lambda (TA + TD + X[v3,z]) + 2 mu X_ii,  sigma_12 += mu TB,
+//                  sigma_13 += mu (TC + X[v1,z]),  sigma_23 += mu (TE + X[v2,z]),  + source      [sub-step B]
+//                  then, on the new stresses still on chip: UA = Y[s13,z], UB = Y[s23,z], UC = Y[s33,z]
+//   AX (x lines):  UA += Y[s11,x], UB += Y[s12,x], UC += Y[s13,x]
+//   AY (y lines):  v1 += b (UA + Y[s12,y]), v2 += b (UB + Y[s22,y]), v3 += b (UC + Y[s23,y])   [sub-step A]
+// X[f,a] = dt * d_a f and Y[f,a] = tau_A * d_a f outside the absorbing layers; inside, the exact integral of the
+// stretched derivative over the sub-step, -PmlAxis::step(...), which also advances that term's memory variable.
+#include <cuda_runtime.h>
+
+#include "../../include/loss.h"
+#include "loss_block.cuh"
+#include "loss_line.cuh"
+#include "loss_types.h"
+
+namespace lossk {
+
+enum { EL_BX = 0, EL_BY = 1, EL_BZ = 2, EL_AX = 3, EL_AY = 4 };
+
+size_t smem_bytes(const LineGeom& g, int nbuf, int nstage, size_t esize);  // loss_kernels_acoustic.cu
+
+// tau times the (stretched) derivative g along this pass's axis at line position pos.
+template <typename T>
+__device__ __forceinline__ T eff(int pml, const PmlAxis<T>& pa, T* mem, int64_t gi, int pos, T g, T tau) {
+  return (pml && pa.in(pos)) ? -pa.step(mem, gi, pos, g) : tau * g;
+}
+
+// Velocity-sub-step term: returns tau * (stretched derivative); in a layer with receiver corrections on, also
+// stores b (X(tau/2) - X(tau)/2), the amount by which the first half of the step differs from half of it.
+template <typename T>
+__device__ __forceinline__ T effA(const ElArgs<T>& a, int term, int64_t gi, int pos, T g, T tau) {
+  if (!(a.pml && a.pA.in(pos))) return tau * g;
+  T xh = T(0);
+  const bool rec = a.dlt[term] != nullptr;
+  if (rec) xh = -a.pA.half(a.memA[term], gi, pos, g);
+  const T xf = -a.pA.step(a.memA[term], gi, pos, g);
+  if (rec) a.dlt[term][gi] = (a.b ? a.b[gi] : a.b0) * (xh - T(0.5) * xf);
+  return xf;
+}
+
+template <typename T, bool KAHAN>
+__device__ __forceinline__ T upd(T* f, T* c, int64_t gi, T delta) {
+  T u = f[gi];
+  if constexpr (KAHAN) {
+    float cc = c[gi];
+    kahan_add(u, cc, delta);
+    c[gi] = cc;
+  } else {
+    u += delta;
+  }
+  f[gi] = u;
+  return u;
+}
+
+template <typename T, int LOGC, bool SFLAV, int PASS, bool KAHAN>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a) {
+  constexpr int C = 1 << LOGC;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, C> cc;
+  const LineGeom& g = a.g;
+  Carve<T> cv(sm, g, 6, 0);
+  T* F[3] = {cv.buf[0], cv.buf[1], cv.buf[2]};
+  T* O[3] = {cv.buf[3], cv.buf[4], cv.buf[5]};
+  const Bundle<LOGC, SFLAV> bun{g.pitch};
+  const WorkMap<SFLAV> wm{g.L, g.p, g.NC};
+  const int logL = SFLAV ? (__ffs(g.L) - 1) : 0;
+  const int nvalid = bundle_bases<SFLAV>(g, blockIdx.x, cv.lb);
+  const int p1 = g.p + 1;
+  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
+  __syncthreads();
+  for (int s = 0; s < 3; ++s) stage_padded<T, SFLAV>(a.src[s], F[s], bun, g, cv.lb, nvalid, logL);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  auto derive = [&](int s) {
+    pmbc_phi<T, 16>(F[s], bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
+    __syncthreads();
+    solve_bundle<T, C, SFLAV>(F[s], O[s], cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
+                              BndPhi<T>{cv.phi, p1});
+  };
+  for (int s = 0; s < 3; ++s) derive(s);
+  const T dt = a.dt, ta = a.acoef;
+  T* const* t = a.tmp;
+  if (PASS == EL_BX) {
+    for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+      const int k = bun.at(l, pos);
+      t[0][gi] = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
+      t[1][gi] = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
+      t[2][gi] = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+    });
+  } else if (PASS == EL_BY) {
+    for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+      const int k = bun.at(l, pos);
+      t[1][gi] += eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
+      t[3][gi] = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
+      t[4][gi] = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+    });
+  } else if (PASS == EL_BZ) {
+    if (a.do_B) {
+      const int outer = blockIdx.x / g.nxb;           // y index of the bundle
+      const int x0 = (blockIdx.x - outer * g.nxb) * g.L;
+      for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+        const int k = bun.at(l, pos);
+        const T x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);  // v1 along z
+        const T x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);  // v2 along z
+        const T x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);  // v3 along z
+        const T xa = t[0][gi], xd = t[3][gi];
+        const T lam = a.lam ? a.lam[gi] : a.lam0;
+        const T mu = a.mu ? a.mu[gi] : a.mu0;
+        const T ltr = lam * (xa + xd + x33);
+        T s11 = ltr + T(2) * mu * xa, s22 = ltr + T(2) * mu * xd, s33 = ltr + T(2) * mu * x33;
+        T s13 = mu * (t[2][gi] + x13);
+        if (a.srcp.on) {
+          const int dz = pos - a.srcp.zs + 12, dy = outer - a.srcp.ys + 12, dx = x0 + l - a.srcp.xs + 12;
+          if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u) {
+            const T sv = (T)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
+            if (a.src_explosive) s11 += sv, s22 += sv, s33 += sv;
+            if (a.src_shear) s13 += sv;
+          }
+        }
+        upd<T, KAHAN>(a.fld[LOSS_FIELD_S11], a.cmp[LOSS_FIELD_S11], gi, s11);
+        upd<T, KAHAN>(a.fld[LOSS_FIELD_S22], a.cmp[LOSS_FIELD_S22], gi, s22);
+        upd<T, KAHAN>(a.fld[LOSS_FIELD_S12], a.cmp[LOSS_FIELD_S12], gi, mu * t[1][gi]);
+        // new stresses needed by the velocity sub-step's z derivatives stay on chip
+        F[0][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S13], a.cmp[LOSS_FIELD_S13], gi, s13);
+        F[1][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S23], a.cmp[LOSS_FIELD_S23], gi, mu * (t[4][gi] + x23));
+        F[2][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S33], a.cmp[LOSS_FIELD_S33], gi, s33);
+      });
+      __syncthreads();
+      if (a.do_A)
+        for (int s = 0; s < 3; ++s) derive(s);
+    }
+    if (a.do_A) {
+      for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+        const int k = bun.at(l, pos);
+        t[5][gi] = effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
+        t[6][gi] = effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
+        t[7][gi] = effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+      });
+    }
+  } else if (PASS == EL_AX) {
+    for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+      const int k = bun.at(l, pos);
+      t[5][gi] += effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
+      t[6][gi] += effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
+      t[7][gi] += effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+    });
+  } else if (PASS == EL_AY) {
+    const int outer = blockIdx.x / g.nxb;  // z index of the bundle
+    const int x0 = (blockIdx.x - outer * g.nxb) * g.L;
+    for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
+      const int k = bun.at(l, pos);
+      const T b = a.b ? a.b[gi] : a.b0;
+      T force = T(0);  // body force f_3 (FORCE_Z source), already multiplied by the sub-step length
+      if (a.srcp.on) {
+        const int dz = outer - a.srcp.zs + 12, dy = pos - a.srcp.ys + 12, dx = x0 + l - a.srcp.xs + 12;
+        if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u)
+          force = (T)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
+      }
+      upd<T, KAHAN>(a.fld[LOSS_FIELD_V1], a.cmp[LOSS_FIELD_V1], gi,
+                    b * (t[5][gi] + effA(a, 0, gi, pos, a.s3h * O[0][k], ta)));
+      upd<T, KAHAN>(a.fld[LOSS_FIELD_V2], a.cmp[LOSS_FIELD_V2], gi,
+                    b * (t[6][gi] + effA(a, 1, gi, pos, a.s3h * O[1][k], ta)));
+      upd<T, KAHAN>(a.fld[LOSS_FIELD_V3], a.cmp[LOSS_FIELD_V3], gi,
+                    b * (t[7][gi] + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + force));
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+template <class K>
+static cudaError_t launch_el_k(K kern, int grid, int threads, size_t smem, cudaStream_t st, void* args) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* argv[] = {args};
+  return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(threads), argv, smem, st);
+}
+
+template <typename T, int PASS, bool KAHAN>
+static cudaError_t launch_el_pass(const ElArgs<T>& a, int logc, int threads, cudaStream_t st) {
+  constexpr bool SF = (PASS == EL_BY || PASS == EL_BZ || PASS == EL_AY);
+  const size_t smem = smem_bytes(a.g, 6, 0, sizeof(T));
+  ElArgs<T> args = a;
+  if (logc == 3 && sizeof(T) == 4) return launch_el_k(k_el<T, 3, SF, PASS, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+  return launch_el_k(k_el<T, 4, SF, PASS, KAHAN>, a.g.nbundles, threads, smem, st, &args);
+}
+
+template <typename T, bool KAHAN>
+cudaError_t launch_el(const ElArgs<T>& a, int pass, int logc, int threads, cudaStream_t st) {
+  switch (pass) {
+    case EL_BX: return launch_el_pass<T, EL_BX, KAHAN>(a, logc, threads, st);
+    case EL_BY: return launch_el_pass<T, EL_BY, KAHAN>(a, logc, threads, st);
+    case EL_BZ: return launch_el_pass<T, EL_BZ, KAHAN>(a, logc, threads, st);
+    case EL_AX: return launch_el_pass<T, EL_AX, KAHAN>(a, logc, threads, st);
+    default: return launch_el_pass<T, EL_AY, KAHAN>(a, logc, threads, st);
+  }
+}
+
+template cudaError_t launch_el<float, false>(const ElArgs<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_el<float, true>(const ElArgs<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_el<double, false>(const ElArgs<double>&, int, int, int, cudaStream_t);
+
+}  // namespace lossk

@@ -68,7 +68,16 @@ struct PmlAxis {
   const T* tab;
   int width;
   int n;
+  const T* tabh;  // the same coefficients for tau / 2 (exact integer-time receiver values), or null
   __device__ __forceinline__ bool in(int i) const { return i < width || i > n - width; }
+  // Increment factor of the first half (tau / 2) of the sub-step, from the memory value before the step; the
+  // memory variable is not changed.  Requires tabh.
+  __device__ __forceinline__ T half(const T* mem, int64_t gi, int i, T g) const {
+    const int n1 = n + 1;
+    const T m0 = mem[gi];
+    const T m1 = tabh[i] * m0 - tabh[n1 + i] * g;
+    return tabh[2 * n1 + i] * (m1 - m0) - tabh[3 * n1 + i] * g;
+  }
   // Advance the memory variable over tau with frozen derivative g; return the field increment factor.
   __device__ __forceinline__ T step(T* mem, int64_t gi, int i, T g) const {
     const int n1 = n + 1;
@@ -102,6 +111,7 @@ struct AcXArgs {
   T* psix;
   T* phix;
   T* phiz;
+  T* dlt;  // v1 receiver correction b (X(dt/2) - X(dt)/2) in the x layers, or null
 };
 
 template <typename T>
@@ -121,6 +131,34 @@ struct AcZArgs {
   int pml;
   PmlAxis<T> zA;
   T* psiz;
+  T* dlt;  // v3 receiver correction in the z layers, or null
+};
+
+// One line pass of the 3-D elastic step (see loss_kernels_elastic.cu).  src: the three fields differentiated
+// along the pass axis; fld/cmp: the nine fields and their compensation terms (LOSS_FIELD_* order); tmp: TA..TE
+// (stress sub-step, 0..4) and UA..UC (velocity sub-step, 5..7); memB/memA: PML memory variables of the three
+// derivative terms of this pass in the stress and velocity sub-steps.
+template <typename T>
+struct ElArgs {
+  LineGeom g;
+  Tables tb;
+  const T* src[3];
+  T* fld[9];
+  T* cmp[9];
+  T* tmp[8];
+  const T* lam;  // or null (then lam0)
+  const T* mu;
+  const T* b;
+  T lam0, mu0, b0;
+  T dt, acoef, s3h, minf;
+  int do_B, do_A;
+  int pml;
+  PmlAxis<T> pB, pA;
+  T* memB[3];
+  T* memA[3];
+  T* dlt[3];  // receiver corrections of the three velocity terms of this pass (in its layers), or null
+  SourceArgs srcp;
+  int src_explosive, src_shear;
 };
 
 }  // namespace lossk

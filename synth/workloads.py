@@ -129,7 +129,7 @@ def acoustic2d_layered(n: int = 2048, p: int = 8, steps: int = 2000, n_nb: int =
 
 
 def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int = 20,
-                          precision: str = "fp32_kahan") -> Workload:
+                          precision: str = "fp32_kahan", pml_width: int = 20) -> Workload:
     """3-D isotropic elastic, vp = 3000, vs = 1730, rho = 2000, explosive plus shear source at the centre,
     15 Hz Ricker, receivers v1, v2, v3 on the top plane."""
     shape = (n + 1,) * 3
@@ -144,12 +144,12 @@ def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int
         name=f"elastic3d_homog_{n}_p{p}", dim=3, physics="elastic", n=(n,) * 3, p=(p,) * 3, h=(h,) * 3,
         n_nb=n_nb, dt=_cfl_dt(h, 3000.0), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
         src_kinds=("explosive", "shear_xz"), f0=f0, t0=1.2 / f0,
-        receivers={"v1": top, "v2": top, "v3": top}, precision=precision)
+        receivers={"v1": top, "v2": top, "v3": top}, precision=precision, pml_width=pml_width)
 
 
 def elastic3d_heterogeneous(n: int = 192, p: int = 4, steps: int = 1500, n_nb: int = 20,
                             precision: str = "fp32_kahan", seeds=(4001, 4002, 4003),
-                            true_model: bool = True) -> Workload:
+                            true_model: bool = True, pml_width: int = 20) -> Workload:
     """3-D elastic with smooth random vp/vs/rho (5 %, 100 m correlation length, clipped so vp/vs >= 1.5).
     ``true_model=False`` gives the homogeneous starting model of the inversion."""
     shape = (n + 1,) * 3
@@ -172,7 +172,7 @@ def elastic3d_heterogeneous(n: int = 192, p: int = 4, steps: int = 1500, n_nb: i
         n_nb=n_nb, dt=_cfl_dt(h, vmax), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
         src_kinds=("explosive", "shear_xz"), f0=f0, t0=1.2 / f0,
         receivers={"v3": _top_row_receivers(shape)}, precision=precision,
-        checkpoint_every=int(math.ceil(math.sqrt(steps))), seed=seeds[0])
+        checkpoint_every=int(math.ceil(math.sqrt(steps))), seed=seeds[0], pml_width=pml_width)
 
 
 def batched_shots(n_shots: int = 64, steps: int = 1500, n_nb: int = 20, seed: int = 5000,

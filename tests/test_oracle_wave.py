@@ -146,7 +146,7 @@ def test_explosive_source_mirror_symmetry():
     """A pure explosive source at the centre of a cubic grid radiates a wavefield symmetric under the swap
     x <-> y: sigma11(z, y, x) = sigma22(z, x, y), v1(z, y, x) = v2(z, x, y), sigma13 <-> sigma23,
     sigma12 symmetric."""
-    w = elastic3d_homogeneous(n=24, p=2, steps=12, n_nb=8)
+    w = elastic3d_homogeneous(n=24, p=2, steps=12, n_nb=8, pml_width=6)
     w.src_kinds = ("explosive",)
     w.receivers = {}
     sim = Simulation(w).step(12, record=False)
