@@ -138,6 +138,47 @@ def _alg_bytes_per_point(kernel, esize, kahan, b_array):
     return n * esize
 
 
+def _batched_leg(torch, pkg, units, warmup_units, k):
+    """The 64-shot survey (n_s from 512 to 2048, M = 128, FP32): tile shapes from the library's autotuner, then
+    timed replays of a captured graph of k batched steps (one persistent launch per kernel per step).  The shots
+    hold ~4.5 GB, far more than L2, so no flush is needed between replays."""
+    from synth import batched_shots
+
+    ws = batched_shots(steps=k)
+    pts = sum(w.points for w in ws)
+    g = pkg.Grid.from_workloads(ws)
+    g.set_schedule(True, k)
+    tune = g.autotune(steps=2)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup_units):
+        g.step(k)
+    g.sync()
+    ev = []
+    for _ in range(units):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.step(k)
+        e1.record(st)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / (units * k)
+    launches = g.profile_read(-1)[1]
+    g.close()
+    peak, kind = _peaks()
+    alg = 40  # B per point-step: x kernel 24 (v1, sigma, kappa, d_z v3 read; sigma, v1 written), z kernel 16
+    value = pts / (ms * 1e-3)
+    return {"workload": f"{len(ws)} shots, n from {min(w.n[0] for w in ws)} to {max(w.n[0] for w in ws)}, M=128, "
+                        f"n_nb=20, PML 40, FP32, graph of {k} steps",
+            "points_per_step": pts, "value": value, "unit": UNIT, "ms_per_step": ms,
+            "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9), "peak_kind": peak_kind_note(kind),
+            "autotune": tune, "launches": launches, "l2": "working set 4.5 GB, no flush"}
+
+
+def peak_kind_note(kind):
+    return "of measured" if kind == "measured" else "of fallback"
+
+
 def run_ours(args):
     import torch
     import paper_2301_05127_gb300 as pkg
@@ -224,6 +265,9 @@ def run_ours(args):
     g64.close()
     g.close()
 
+    # --- batched multi-shot survey ----------------------------------------------------------------------------
+    batched = _batched_leg(torch, pkg, units=3, warmup_units=1, k=10) if not args.no_batched else None
+
     # --- end to end through the public API with host buffers ---------------------------------------------
     ge = pkg.Grid.from_workloads([w])
     shape = w.shape
@@ -264,6 +308,7 @@ def run_ours(args):
             "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + args.steps},
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms},
+            "batched": batched,
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s_timed_region": t_wall,
@@ -317,6 +362,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-shot batched leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -187,6 +187,7 @@ enum {
   LOSS_KERNEL_ELASTIC_X = 4,  /* 3-D elastic passes on x lines */
   LOSS_KERNEL_ELASTIC_Y = 5,  /* 3-D elastic passes on y lines */
   LOSS_KERNEL_ELASTIC_Z = 6,  /* 3-D elastic passes on z lines */
+  LOSS_KERNEL_CLOCK = 7,      /* batched schedule: end-of-step advance of the device step counters */
   LOSS_NUM_KERNELS = 16
 };
 
@@ -195,6 +196,42 @@ enum {
  * (3 or 4; FP64 grids always use 4); 0 = the built-in choice.  Applies to every shot; shapes that do not fit
  * fall back to smaller bundles at launch.  Used by the autotuner. */
 loss_status_t loss_set_launch(loss_handle_t handle, int32_t kernel, int32_t lines_per_block, int32_t chunk_log2);
+
+/* Tile shape of one kernel family given as a block size: threads_per_block (32..1024, 512 at most for FP64 grids)
+ * is the thread count a block of this kernel aims at; every shot then takes the widest power-of-two bundle of
+ * whole lines whose chunks fit in it (so shots of different sizes share one block size in a batched launch).
+ * chunk_log2 as in loss_set_launch.  0 = the built-in choice.  An explicit lines_per_block (loss_set_launch)
+ * takes precedence.  Used by the autotuner.  LOSS_E_ARG for values out of range. */
+loss_status_t loss_set_tile(loss_handle_t handle, int32_t kernel, int32_t threads_per_block, int32_t chunk_log2);
+
+/* Schedule of loss_step (spec batching pattern; the paper's MPI design runs one process per patch instead).
+ * batched != 0 (the default): a handle whose shots are all 2-D acoustic grids of one precision advances them
+ * together, each step being one persistent launch of the x kernel and one of the z kernel over the tiles of all
+ * shots (a tile = one bundle of whole lines of one shot), one launch per receiver phase and a clock tick.  The
+ * source amplitude and the trace row of each step are read from per-shot device counters, so the launches of
+ * every step are identical.  graph_steps > 0: such handles (also with a single shot) capture graph_steps steps
+ * once in a CUDA graph and replay it (the remainder of a loss_step call runs as plain launches); the graph is
+ * captured again when shapes, buffers or the shot set change.  Results are those of the per-shot schedule.
+ * Other handles (3-D elastic) always use per-shot launches.  Per-kernel timing (loss_profile) is not available
+ * for steps replayed from a graph; launches are counted.  LOSS_E_ARG if graph_steps < 0. */
+loss_status_t loss_set_schedule(loss_handle_t handle, int32_t batched, int32_t graph_steps);
+
+/* One autotuner result: the tile shape chosen for a kernel family and its measured mean launch time. */
+typedef struct {
+  int32_t kernel;            /* LOSS_KERNEL_* */
+  int32_t threads_per_block; /* as loss_set_tile */
+  int32_t chunk_log2;
+  double ms;                 /* mean device time of one launch of the chosen shape */
+} loss_tune_entry_t;
+
+/* Project-written autotuner (spec batching pattern): times every candidate tile shape (threads per block
+ * 128..1024, chunk_log2 3 or 4) of each kernel family the handle's time step uses, on a scratch copy of the
+ * handle (same grids, models, absorbing layers and schedule; zero fields), with `steps` timed steps per candidate
+ * after one warm-up step, and applies the fastest shape of each family to the handle (loss_set_tile).  The
+ * handle's own state is not touched.  out (capacity cap entries, may be NULL) receives one entry per tuned
+ * family and *n_out their number.  Needs device memory for a second copy of the handle's arrays.
+ * Returns LOSS_E_ARG for steps < 1, the error of the first failing call otherwise. */
+loss_status_t loss_autotune(loss_handle_t handle, int32_t steps, loss_tune_entry_t* out, int32_t cap, int32_t* n_out);
 
 /* Reset the per-kernel counters of the handle and switch CUDA-event timing of every kernel launch on
  * (enable != 0) or off.  Launches are always counted. */

@@ -43,6 +43,11 @@ class Allocator(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("threads_per_block", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
 _lib = None
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
@@ -71,11 +76,15 @@ _PROTOS = {
     "loss_sync": (_I32, [_H]),
     "loss_derivative_noalloc": (_I32, [ctypes.POINTER(GridDesc), _I32, _P, _P, _P]),
     "loss_set_launch": (_I32, [_H, _I32, _I32, _I32]),
+    "loss_set_tile": (_I32, [_H, _I32, _I32, _I32]),
+    "loss_set_schedule": (_I32, [_H, _I32, _I32]),
+    "loss_autotune": (_I32, [_H, _I32, ctypes.POINTER(TuneEntry), _I32, ctypes.POINTER(_I32)]),
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
 KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
-           "elastic_z": 6}
+           "elastic_z": 6, "clock": 7}
+KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
 def lib():
@@ -309,6 +318,22 @@ class Grid:
     def set_launch(self, kernel, lines_per_block=0, chunk_log2=0):
         kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         _check(lib().loss_set_launch(self.h, kid, int(lines_per_block), int(chunk_log2)), self.h)
+
+    def set_tile(self, kernel, threads_per_block=0, chunk_log2=0):
+        kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        _check(lib().loss_set_tile(self.h, kid, int(threads_per_block), int(chunk_log2)), self.h)
+
+    def set_schedule(self, batched: bool = True, graph_steps: int = 0):
+        _check(lib().loss_set_schedule(self.h, 1 if batched else 0, int(graph_steps)), self.h)
+
+    def autotune(self, steps: int = 3) -> Dict[str, dict]:
+        """Run the library's autotuner; returns {kernel name: {threads_per_block, chunk_log2, ms}}."""
+        out = (TuneEntry * 16)()
+        n = _I32()
+        _check(lib().loss_autotune(self.h, int(steps), out, 16, ctypes.byref(n)), self.h)
+        return {KERNEL_NAMES.get(e.kernel, str(e.kernel)): {"threads_per_block": e.threads_per_block,
+                                                            "chunk_log2": e.chunk_log2, "ms": e.ms}
+                for e in out[:n.value]}
 
     def profile(self, enable: bool = True):
         _check(lib().loss_profile(self.h, 1 if enable else 0), self.h)

@@ -168,9 +168,10 @@ static int axis_slot(const Shot& s, int axis) {
 
 // Build the launch geometry of lines along internal slot `k` for an array with strides (sz, sy, 1).
 // nbuf padded line buffers and nstage dense row-staging buffers (X flavour) per block; want_L > 0 requests a
-// bundle width (lines per block).
+// bundle width (lines per block); otherwise want_threads > 0 requests the widest power-of-two bundle whose chunks
+// fit in that many threads.
 loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc,
-                        int* threads, int nbuf, int nstage, int want_L, int want_logc) {
+                        int* threads, int nbuf, int nstage, int want_L, int want_logc, int want_threads) {
   const int n = (int)s.n[k];
   const int p = s.p[k];
   const int M = n / p;
@@ -188,7 +189,11 @@ loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t s
   G.mmagic = (unsigned)((((uint64_t)1 << 32) + (uint64_t)M - 1) / (uint64_t)M);
   const int per_line = p * G.NC;
   const size_t es = s.esize;
-  const size_t smax = (size_t)h->smem_optin - 2048;  // headroom for the kernels' static shared memory
+  const size_t smax = (size_t)h->smem_optin - 4096;  // headroom for the kernels' static shared memory
+  if (want_L <= 0 && want_threads > 0) {
+    want_L = 1;
+    while (want_L < 32 && 2 * want_L * per_line <= want_threads) want_L *= 2;
+  }
   const int np_pad = (n + (n >> *logc)) + 1;  // padpos(n) + 1
   const int vec = (int)(16 / es);
   G.spitch = ((n + 1 + vec - 1) / vec) * vec;
@@ -470,6 +475,7 @@ loss_status_t loss_destroy(loss_handle_t h) {
   if (!h) return LOSS_OK;
   cudaStreamSynchronize(h->stream);
   drop_events(h);
+  batch_destroy(h);
   std::vector<void*> owned = h->owned;
   for (void* p : owned) dev_free(h, p);
   cudaStreamSynchronize(h->stream);
@@ -485,6 +491,128 @@ loss_status_t loss_set_launch(loss_handle_t h, int32_t kernel, int32_t lines_per
     return fail(h, LOSS_E_ARG, "lines_per_block must be 0 or a power of two <= 32");
   h->lines_per_block[kernel] = lines_per_block;
   h->chunk_log2[kernel] = chunk_log2;
+  return LOSS_OK;
+}
+
+loss_status_t loss_set_tile(loss_handle_t h, int32_t kernel, int32_t threads_per_block, int32_t chunk_log2) {
+  LOSS_TRY(guard(h));
+  if (chunk_log2 != 0 && chunk_log2 != 3 && chunk_log2 != 4) return fail(h, LOSS_E_ARG, "chunk_log2 must be 0, 3 or 4");
+  if (kernel < 0 || kernel >= LOSS_NUM_KERNELS) return fail(h, LOSS_E_ARG, "kernel id out of range");
+  if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 1024))
+    return fail(h, LOSS_E_ARG, "threads_per_block must be 0 or in 32..1024");
+  h->tile_threads[kernel] = threads_per_block;
+  h->chunk_log2[kernel] = chunk_log2;
+  return LOSS_OK;
+}
+
+loss_status_t loss_set_schedule(loss_handle_t h, int32_t batched, int32_t graph_steps) {
+  LOSS_TRY(guard(h));
+  if (graph_steps < 0) return fail(h, LOSS_E_ARG, "graph_steps must be >= 0");
+  h->batched = batched != 0;
+  h->graph_steps = graph_steps;
+  if (graph_steps == 0) batch_release(h);
+  return LOSS_OK;
+}
+
+loss_status_t loss_autotune(loss_handle_t h, int32_t steps, loss_tune_entry_t* out, int32_t cap, int32_t* n_out) {
+  LOSS_TRY(guard(h));
+  if (steps < 1) return fail(h, LOSS_E_ARG, "steps must be >= 1");
+  if (n_out) *n_out = 0;
+  bool ac = false, el = false, fp64 = false;
+  for (const Shot& s : h->shots) {
+    if (!s.has_model) return fail(h, LOSS_E_STATE, "loss_set_model must be called for every shot before tuning");
+    ac = ac || s.d.physics == LOSS_ACOUSTIC;
+    el = el || s.d.physics == LOSS_ELASTIC;
+    fp64 = fp64 || s.esize == 8;
+  }
+  std::vector<int> kids;
+  if (ac) kids.insert(kids.end(), {LOSS_KERNEL_ACOUSTIC_X, LOSS_KERNEL_ACOUSTIC_Z});
+  if (el) kids.insert(kids.end(), {LOSS_KERNEL_ELASTIC_X, LOSS_KERNEL_ELASTIC_Y, LOSS_KERNEL_ELASTIC_Z});
+  // candidates: (threads, chunk_log2)
+  std::vector<std::pair<int, int>> cand;
+  for (int lc : {3, 4}) {
+    if (fp64 && lc == 3) continue;
+    for (int t : {128, 256, 512, 1024})
+      if (!(fp64 && t > 512)) cand.push_back({t, lc});
+  }
+  // scratch copy: same grids, models, layers, source and schedule; zero fields
+  std::vector<loss_grid_desc_t> descs;
+  for (const Shot& s : h->shots) descs.push_back(s.d);
+  loss_handle_t t = nullptr;
+  LOSS_TRY(loss_create_grid(descs.data(), (int32_t)descs.size(), h->has_alloc ? &h->alloc : nullptr,
+                            (void*)h->stream, &t));
+  struct Drop {
+    loss_handle_t t;
+    ~Drop() { loss_destroy(t); }
+  } drop{t};
+  auto relay = [&](loss_status_t st) {
+    if (st != LOSS_OK) h->err = "autotune: " + t->err;
+    return st;
+  };
+  for (size_t i = 0; i < h->shots.size(); ++i) {
+    const Shot& a = h->shots[i];
+    Shot& b = t->shots[i];
+    for (int m = 0; m < 3; ++m)
+      if (a.model[m] && b.model[m])
+        LOSS_TRY(cuda_check(h, cudaMemcpyAsync(b.model[m], a.model[m], (size_t)a.total * a.esize,
+                                               cudaMemcpyDeviceToDevice, h->stream), "copy model"));
+    b.has_model = true;
+    b.vmax = a.vmax;
+    b.b_const = a.b_const;
+    b.b0 = a.b0;
+    b.lam_const = a.lam_const;
+    b.mu_const = a.mu_const;
+    b.lam0 = a.lam0;
+    b.mu0 = a.mu0;
+    if (a.pml_on) LOSS_TRY(relay(loss_set_pml(t, (int32_t)i, a.pml_width, a.pml_R, a.pml_kmax, a.pml_f0)));
+    b.src_on = a.src_on;
+    b.src_kinds = a.src_kinds;
+    for (int k = 0; k < 3; ++k) b.src_idx[k] = a.src_idx[k];
+    b.src_amp = a.src_amp;
+    b.src_f0 = a.src_f0;
+    b.src_t0 = a.src_t0;
+    b.src_norm = a.src_norm;
+    for (int k = 0; k < 25; ++k) b.src_g[k] = a.src_g[k];
+  }
+  t->batched = h->batched;
+  t->graph_steps = 0;  // plain launches, so that every kernel can be timed
+  for (int k = 0; k < LOSS_NUM_KERNELS; ++k) {
+    t->tile_threads[k] = h->tile_threads[k];
+    t->chunk_log2[k] = h->chunk_log2[k];
+  }
+  const double inf = 1e300;
+  std::vector<double> best(kids.size(), inf);
+  std::vector<int> best_c(kids.size(), -1);
+  for (size_t c = 0; c < cand.size(); ++c) {
+    for (int kid : kids) {
+      t->lines_per_block[kid] = 0;
+      t->tile_threads[kid] = cand[c].first;
+      t->chunk_log2[kid] = cand[c].second;
+    }
+    loss_status_t st = loss_step(t, 1);
+    if (st == LOSS_E_UNSUPPORTED) continue;  // a shape that does not fit this grid
+    LOSS_TRY(relay(st));
+    LOSS_TRY(relay(loss_profile(t, 1)));
+    LOSS_TRY(relay(loss_step(t, steps)));
+    for (size_t f = 0; f < kids.size(); ++f) {
+      double ms = 0.0;
+      int64_t nl = 0;
+      LOSS_TRY(relay(loss_profile_read(t, kids[f], &ms, &nl)));
+      const double per_step = nl ? ms / steps : inf;
+      if (per_step < best[f]) best[f] = per_step, best_c[f] = (int)c;
+    }
+    LOSS_TRY(relay(loss_profile(t, 0)));
+  }
+  int32_t n = 0;
+  for (size_t f = 0; f < kids.size(); ++f) {
+    if (best_c[f] < 0) continue;
+    h->lines_per_block[kids[f]] = 0;
+    h->tile_threads[kids[f]] = cand[best_c[f]].first;
+    h->chunk_log2[kids[f]] = cand[best_c[f]].second;
+    if (out && n < cap) out[n] = loss_tune_entry_t{kids[f], cand[best_c[f]].first, cand[best_c[f]].second, best[f]};
+    ++n;
+  }
+  if (n_out) *n_out = n;
   return LOSS_OK;
 }
 
@@ -784,6 +912,7 @@ loss_status_t loss_step(loss_handle_t h, int64_t n_steps) {
     if (!s.has_model) return fail(h, LOSS_E_STATE, "loss_set_model must be called for every shot before stepping");
   }
   for (Shot& s : h->shots) LOSS_TRY(ensure_trace_capacity(h, s, s.rcv_steps + n_steps));
+  if (batch_eligible(h)) return step_batched(h, n_steps);
   for (int64_t k = 0; k < n_steps; ++k) {
     for (Shot& s : h->shots) LOSS_TRY(step_shot(h, s));
   }
@@ -957,7 +1086,7 @@ static loss_status_t run_derivative_t(loss_ctx* h, Shot& s, int k, const T* f, T
   LineGeom g;
   int logc, threads;
   LOSS_TRY(line_geom(h, s, k, sz, sy, &g, &logc, &threads, d2 ? 3 : 2, 0, h->lines_per_block[LOSS_KERNEL_DERIVATIVE],
-                     h->chunk_log2[LOSS_KERNEL_DERIVATIVE]));
+                     h->chunk_log2[LOSS_KERNEL_DERIVATIVE], h->tile_threads[LOSS_KERNEL_DERIVATIVE]));
   DerivArgs<T> a{};
   a.g = g;
   a.tb = tables_for<T>(h, s, k);

@@ -62,6 +62,36 @@ struct Shot {
   // time stepping
   int64_t step = 0;
   bool staggered = false;  // velocities hold v at t_step + dt/2 instead of t_step
+  // per-step source amplitudes for launches that read them from the device (batched / graph schedule)
+  double* amp_tab = nullptr;
+  int64_t amp_cap = 0;
+  double amp_sig[5] = {};  // dt, norm, f0, t0, kinds the table was built for
+};
+
+// Device tables and launch shapes of the batched schedule (one persistent launch per kernel over all shots).
+struct BatchState {
+  void* xtab = nullptr;   // AcXArgs[n_shots]
+  void* ztab = nullptr;   // AcZArgs[n_shots]
+  int* tile0 = nullptr;   // [2][n_shots + 1]: first tile of each shot, X then Z
+  void* jobs = nullptr;   // GatherJob[pre jobs + post jobs]
+  StepClock* clk = nullptr;
+  size_t cap_bytes[4] = {};  // allocated bytes of xtab, ztab, tile0, jobs
+  int clk_cap = 0;
+  std::vector<unsigned char> host[4];  // last uploaded contents of xtab, ztab, tile0, jobs
+  int xthreads = 0, zthreads = 0, xlogc = 0, zlogc = 0;
+  size_t xsmem = 0, zsmem = 0;
+  int xtiles = 0, ztiles = 0;
+  int xgrid = 0, zgrid = 0;  // persistent grid sizes
+  std::vector<unsigned char> clk_host;  // clocks the device holds after the last batched call
+  int npre = 0, npost = 0;
+  int64_t pre_max = 0, post_max = 0;
+  // captured graph of graph_k batched steps and the launch signature it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (the legacy default stream of the
+                                      // handle cannot be captured); replays go to the handle's stream
+  int64_t graph_k = 0;
+  std::vector<int64_t> gsig;
+  int64_t graph_launches[LOSS_NUM_KERNELS] = {};  // kernel launches in one replay
 };
 
 }  // namespace lossk
@@ -81,6 +111,12 @@ struct loss_ctx {
   float* t32 = nullptr;
   int lines_per_block[LOSS_NUM_KERNELS] = {};  // 0 = built-in choice (loss_set_launch)
   int chunk_log2[LOSS_NUM_KERNELS] = {};
+  int tile_threads[LOSS_NUM_KERNELS] = {};     // 0 = built-in choice (loss_set_tile)
+  // schedule (loss_set_schedule)
+  int batched = 1;       // several 2-D acoustic shots: one persistent launch per kernel over all of them
+  int graph_steps = 0;   // > 0: steps are replayed from a captured CUDA graph of this many steps
+  bool capturing = false;
+  lossk::BatchState batch;
   // launch accounting (loss_profile / loss_profile_read)
   int64_t launches[LOSS_NUM_KERNELS] = {};
   bool prof = false;
@@ -98,7 +134,7 @@ loss_status_t cuda_check(loss_ctx* h, cudaError_t e, const char* what);
 loss_status_t dev_alloc(loss_ctx* h, size_t bytes, void** out);
 void dev_free(loss_ctx* h, void* p);
 loss_status_t line_geom(loss_ctx* h, const Shot& s, int k, int64_t sz, int64_t sy, LineGeom* g, int* logc, int* threads,
-                        int nbuf, int nstage, int want_L, int want_logc);
+                        int nbuf, int nstage, int want_L, int want_logc, int want_threads = 0);
 bool field_used(const Shot& s, int f);
 void shot_geometry(Shot& s);
 loss_status_t validate(const loss_grid_desc_t& d, std::string* why);
@@ -115,7 +151,7 @@ struct LaunchScope {
   cudaEvent_t a = nullptr, b = nullptr;
   LaunchScope(loss_ctx* hh, int k) : h(hh), kernel(k) {
     ++h->launches[k];
-    if (h->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+    if (h->prof && !h->capturing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
       cudaEventRecord(a, h->stream);
   }
   ~LaunchScope() {
@@ -129,6 +165,10 @@ struct LaunchScope {
 // loss_step.cu
 loss_status_t step_shot(loss_ctx* h, Shot& s);
 loss_status_t unstagger(loss_ctx* h, Shot& s);
+bool batch_eligible(const loss_ctx* h);
+loss_status_t step_batched(loss_ctx* h, int64_t n_steps);
+void batch_release(loss_ctx* h);
+void batch_destroy(loss_ctx* h);
 
 // kernels
 size_t smem_bytes(const LineGeom& g, int nbuf, int nstage, size_t esize);
@@ -143,5 +183,18 @@ cudaError_t launch_el(const ElArgs<T>& a, int pass, int logc, int threads, cudaS
 template <typename T>
 cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, const T* d0, const T* d1,
                           const T* d2, cudaStream_t st);
+template <typename T, bool KAHAN>
+cudaError_t batch_grid_ac_x(int logc, int threads, size_t smem, int ntiles, int num_sms, int* grid);
+template <typename T, bool KAHAN>
+cudaError_t batch_grid_ac_z(int logc, int threads, size_t smem, int ntiles, int num_sms, int* grid);
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_x_batch(const AcXArgs<T>* tab, const int* tile0, int nshots, int ntiles, int logc, int threads,
+                              size_t smem, int grid, cudaStream_t st);
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshots, int ntiles, int logc, int threads,
+                              size_t smem, int grid, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
+cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
 
 }  // namespace lossk

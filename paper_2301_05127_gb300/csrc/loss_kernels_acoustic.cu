@@ -96,12 +96,37 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_deriv(DerivArgs
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// X kernel of the 2-D acoustic step: sub-step B on whole x lines, then the x part of sub-step A.
+// Source amplitude of this step: the immediate value, or the entry of the per-step table at the device clock.
+__device__ __forceinline__ double source_amp(const SourceArgs& s) {
+  return s.amp_tab ? s.amp_tab[s.clk->step] : s.amp;
+}
+
+// Shot of tile t in a batched launch: the last s with tile0[s] <= t (tile0 ascending, tile0[0] = 0).
+__device__ __forceinline__ int tile_shot(const int* __restrict__ tile0, int nshots, int t) {
+  int lo = 0, hi = nshots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile0[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block-wide copy of one shot's launch descriptor into shared memory.
+template <class A>
+__device__ __forceinline__ void copy_args(A* dst, const A* __restrict__ src) {
+  static_assert(sizeof(A) % 8 == 0, "descriptor size");
+  const uint64_t* s = reinterpret_cast<const uint64_t*>(src);
+  uint64_t* d = reinterpret_cast<uint64_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(A) / 8); i += blockDim.x) d[i] = s[i];
+}
+
+// X kernel of the 2-D acoustic step: sub-step B on whole x lines, then the x part of sub-step A.  One tile is
+// one bundle `bid` of rows; cc must hold the chunk classes of this geometry.
 template <typename T, int LOGC, bool KAHAN>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T> a) {
+__device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned char* sm,
+                                          const ChunkClasses<T, 1 << LOGC>& cc) {
   constexpr int C = 1 << LOGC;
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ ChunkClasses<T, C> cc;
   const LineGeom& g = a.g;
   Carve<T> cv(sm, g, 3, 4);
   T* V = cv.buf[0];  // v1 (old)
@@ -113,10 +138,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T>
   T* SV = cv.stg[3];  // compensation of v1
   const Bundle<LOGC, false> bun{g.pitch};
   const WorkMap<false> wm{g.L, g.p, g.NC};
-  const int nvalid = bundle_bases<false>(g, blockIdx.x, cv.lb);
+  const int nvalid = bundle_bases<false>(g, bid, cv.lb);
   const int p1 = g.p + 1;
   const int sp = g.spitch;
-  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
+  const double amp = source_amp(a.src);
+  const bool son = a.src.on && amp != 0.0;
   __syncthreads();
   stage_padded<T, false>(a.v1, V, bun, g, cv.lb, nvalid, 0);
   stage_padded<T, false>(a.sigma, D, bun, g, cv.lb, nvalid, 0);
@@ -137,12 +163,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T>
                               BndPhi<T>{cv.phi, p1});
     cp_async_wait<0>();
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * g.L;
+    const int64_t r0 = (int64_t)bid * g.L;
     const int np = g.n + 1;
     for (int l = 0; l < nvalid; ++l) {
       const int z = (int)((r0 + l) / g.ny1);
       const bool zlay = a.pml && a.zB.in(z);
-      const bool srow = a.src.on && (unsigned)(z - a.src.zs + 12) < 25u;
+      const bool srow = son && (unsigned)(z - a.src.zs + 12) < 25u;
       const int64_t rb = cv.lb[l];
       const T* stl = ST + l * sp;
       const T* skl = SK + l * sp;
@@ -157,7 +183,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T>
         T delta = skl[pos] * inc;
         if (srow) {
           const int dx = pos - a.src.xs + 12;
-          if ((unsigned)dx < 25u) delta += (T)(a.src.amp * a.src.g[z - a.src.zs + 12] * a.src.g[dx]);
+          if ((unsigned)dx < 25u) delta += (T)(amp * a.src.g[z - a.src.zs + 12] * a.src.g[dx]);
         }
         const int k = bun.at(l, pos);
         T sg = D[k];
@@ -283,12 +309,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T>
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Z kernel of the 2-D acoustic step: z part of sub-step A on whole z lines, then tmp = d_z v3.
+// Z kernel of the 2-D acoustic step: z part of sub-step A on whole z lines, then tmp = d_z v3.  One tile is one
+// bundle `bid` of neighbouring z lines.
 template <typename T, int LOGC, bool KAHAN>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T> a) {
+__device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned char* sm,
+                                          const ChunkClasses<T, 1 << LOGC>& cc) {
   constexpr int C = 1 << LOGC;
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ ChunkClasses<T, C> cc;
   const LineGeom& g = a.g;
   Carve<T> cv(sm, g, 2, 0);
   T* S = cv.buf[0];  // sigma, then v3 (new)
@@ -296,10 +322,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T>
   const Bundle<LOGC, true> bun{g.pitch};
   const WorkMap<true> wm{g.L, g.p, g.NC};
   const int logL = log2_pow2(g.L);
-  const int nvalid = bundle_bases<true>(g, blockIdx.x, cv.lb);
+  const int nvalid = bundle_bases<true>(g, bid, cv.lb);
   const int np = g.n + 1;
   const int p1 = g.p + 1;
-  chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
   __syncthreads();
   {
     // L2 prefetch of the bundle's segments of every array read later (segments of L elements start on
@@ -399,8 +424,75 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T>
 }
 
 // ---------------------------------------------------------------------------------------------------------------
-// Receiver gather: mode 0 out[r] = f[idx[r]]; mode 1 out[r] = (out[r] + f[idx[r]]) / 2 (integer-time velocity
-// from the two staggered half-step values).
+// Kernels: one launch per shot (a tile per block), and one persistent launch over the tiles of all shots of a
+// handle (tile t of the concatenated tile list; the block copies the shot's descriptor into shared memory and
+// rebuilds its chunk classes when the shot changes).  The batched kernels read the descriptor from shared memory
+// instead of the parameter bank, which costs registers, so their blocks are capped at kBatchThreads threads.
+template <typename T, int LOGC, bool KAHAN>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_x(AcXArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, 1 << LOGC> cc;
+  chunk_classes_init<T, 1 << LOGC>(&cc, a.g.M, a.g.NC, a.tb.t32, a.tb.t64, a.minf);
+  ac_x_tile<T, LOGC, KAHAN>(a, blockIdx.x, sm, cc);
+}
+
+template <typename T, int LOGC, bool KAHAN>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_ac_z(AcZArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, 1 << LOGC> cc;
+  chunk_classes_init<T, 1 << LOGC>(&cc, a.g.M, a.g.NC, a.tb.t32, a.tb.t64, a.minf);
+  ac_z_tile<T, LOGC, KAHAN>(a, blockIdx.x, sm, cc);
+}
+
+template <typename T, int LOGC, bool KAHAN>
+__global__ void __launch_bounds__(kBatchThreads)
+    k_ac_x_batch(const AcXArgs<T>* __restrict__ tab, const int* __restrict__ tile0, int nshots, int ntiles) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, 1 << LOGC> cc;
+  __shared__ __align__(16) unsigned char sa_raw[sizeof(AcXArgs<T>)];
+  __shared__ int s_shot;
+  AcXArgs<T>& sa = *reinterpret_cast<AcXArgs<T>*>(sa_raw);
+  int cur = -1;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0) s_shot = tile_shot(tile0, nshots, t);
+    __syncthreads();
+    const int shot = s_shot;
+    if (shot != cur) {
+      copy_args(&sa, tab + shot);
+      __syncthreads();
+      chunk_classes_init<T, 1 << LOGC>(&cc, sa.g.M, sa.g.NC, sa.tb.t32, sa.tb.t64, sa.minf);
+      cur = shot;
+    }
+    ac_x_tile<T, LOGC, KAHAN>(sa, t - tile0[shot], sm, cc);
+    __syncthreads();
+  }
+}
+
+template <typename T, int LOGC, bool KAHAN>
+__global__ void __launch_bounds__(kBatchThreads)
+    k_ac_z_batch(const AcZArgs<T>* __restrict__ tab, const int* __restrict__ tile0, int nshots, int ntiles) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ ChunkClasses<T, 1 << LOGC> cc;
+  __shared__ __align__(16) unsigned char sa_raw[sizeof(AcZArgs<T>)];
+  __shared__ int s_shot;
+  AcZArgs<T>& sa = *reinterpret_cast<AcZArgs<T>*>(sa_raw);
+  int cur = -1;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0) s_shot = tile_shot(tile0, nshots, t);
+    __syncthreads();
+    const int shot = s_shot;
+    if (shot != cur) {
+      copy_args(&sa, tab + shot);
+      __syncthreads();
+      chunk_classes_init<T, 1 << LOGC>(&cc, sa.g.M, sa.g.NC, sa.tb.t32, sa.tb.t64, sa.minf);
+      cur = shot;
+    }
+    ac_z_tile<T, LOGC, KAHAN>(sa, t - tile0[shot], sm, cc);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------------
 // Receiver gather.  mode 0: out[r] = f[idx[r]].  mode 1 (velocities, staggered state): out holds v_{n+1/2} and
 // f holds v_{n+3/2}; the integer-time value is v_{n+1/2} + (v_{n+3/2} - v_{n+1/2}) / 2 plus, inside absorbing
 // layers where the exponential sub-flow is not linear in the step length, the corrections d0..d2 (may be null).
@@ -419,6 +511,35 @@ __global__ void k_gather(const T* __restrict__ f, const int64_t* __restrict__ id
       if (d2) c += d2[q];
       out[r] = out[r] + T(0.5) * (v - out[r]) + c;
     }
+  }
+}
+
+// All receiver gathers of one phase of a batched step: job blockIdx.y, trace row from the shot's device clock.
+template <typename T>
+__global__ void k_gather_batch(const GatherJob<T>* __restrict__ jobs) {
+  const GatherJob<T>& j = jobs[blockIdx.y];
+  T* out = j.trace + j.clk->row * j.n_rcv + j.off;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < j.cnt; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = j.idx[r];
+    const T v = j.f[q];
+    if (j.mode == 0) {
+      out[r] = v;
+    } else {
+      T c = T(0);
+      if (j.d[0]) c += j.d[0][q];
+      if (j.d[1]) c += j.d[1][q];
+      if (j.d[2]) c += j.d[2][q];
+      out[r] = out[r] + T(0.5) * (v - out[r]) + c;
+    }
+  }
+}
+
+// End of a batched step: advance every shot's device clock.
+__global__ void k_tick(StepClock* __restrict__ c, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    c[i].step += 1;
+    c[i].row += c[i].row_inc;
   }
 }
 
@@ -474,6 +595,67 @@ cudaError_t launch_ac_z(const AcZArgs<T>& a, int logc, int threads, cudaStream_t
   return launch(k_ac_z<T, 4, KAHAN>, a.g.nbundles, threads, smem, st, &args);
 }
 
+// Persistent launches: as many blocks as fit on the device at once (at most one per tile), each looping over
+// tiles.  The grid size and the shared-memory attribute are set up front (outside any graph capture).
+template <class K>
+static cudaError_t persistent_grid(K kern, int ntiles, int threads, size_t smem, int num_sms, int* grid) {
+  *grid = 0;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = ntiles < per_sm * num_sms ? ntiles : per_sm * num_sms;
+  return cudaSuccess;
+}
+
+template <typename T, bool KAHAN>
+cudaError_t batch_grid_ac_x(int logc, int threads, size_t smem, int ntiles, int num_sms, int* grid) {
+  if (logc == 3 && sizeof(T) == 4) return persistent_grid(k_ac_x_batch<T, 3, KAHAN>, ntiles, threads, smem, num_sms, grid);
+  return persistent_grid(k_ac_x_batch<T, 4, KAHAN>, ntiles, threads, smem, num_sms, grid);
+}
+
+template <typename T, bool KAHAN>
+cudaError_t batch_grid_ac_z(int logc, int threads, size_t smem, int ntiles, int num_sms, int* grid) {
+  if (logc == 3 && sizeof(T) == 4) return persistent_grid(k_ac_z_batch<T, 3, KAHAN>, ntiles, threads, smem, num_sms, grid);
+  return persistent_grid(k_ac_z_batch<T, 4, KAHAN>, ntiles, threads, smem, num_sms, grid);
+}
+
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_x_batch(const AcXArgs<T>* tab, const int* tile0, int nshots, int ntiles, int logc, int threads,
+                              size_t smem, int grid, cudaStream_t st) {
+  if (ntiles <= 0 || grid <= 0) return cudaSuccess;
+  void* argv[] = {(void*)&tab, (void*)&tile0, (void*)&nshots, (void*)&ntiles};
+  const void* kern = (logc == 3 && sizeof(T) == 4) ? (const void*)k_ac_x_batch<T, 3, KAHAN>
+                                                    : (const void*)k_ac_x_batch<T, 4, KAHAN>;
+  return cudaLaunchKernel(kern, dim3(grid), dim3(threads), argv, smem, st);
+}
+
+template <typename T, bool KAHAN>
+cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshots, int ntiles, int logc, int threads,
+                              size_t smem, int grid, cudaStream_t st) {
+  if (ntiles <= 0 || grid <= 0) return cudaSuccess;
+  void* argv[] = {(void*)&tab, (void*)&tile0, (void*)&nshots, (void*)&ntiles};
+  const void* kern = (logc == 3 && sizeof(T) == 4) ? (const void*)k_ac_z_batch<T, 3, KAHAN>
+                                                    : (const void*)k_ac_z_batch<T, 4, KAHAN>;
+  return cudaLaunchKernel(kern, dim3(grid), dim3(threads), argv, smem, st);
+}
+
+template <typename T>
+cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st) {
+  if (njobs <= 0 || max_cnt <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t bx = (max_cnt + threads - 1) / threads;
+  k_gather_batch<T><<<dim3((unsigned)(bx < 1024 ? bx : 1024), (unsigned)njobs), threads, 0, st>>>(jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st) {
+  k_tick<<<(n + 127) / 128, 128, 0, st>>>(c, n);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_gather(const T* f, const int64_t* idx, int64_t n, T* out, int mode, const T* d0, const T* d1,
                           const T* d2, cudaStream_t st) {
@@ -492,6 +674,26 @@ template cudaError_t launch_ac_x<double, false>(const AcXArgs<double>&, int, int
 template cudaError_t launch_ac_z<float, false>(const AcZArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_ac_z<float, true>(const AcZArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_ac_z<double, false>(const AcZArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_ac_x_batch<float, false>(const AcXArgs<float>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t launch_ac_x_batch<float, true>(const AcXArgs<float>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t launch_ac_x_batch<double, false>(const AcXArgs<double>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t launch_ac_z_batch<float, false>(const AcZArgs<float>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t launch_ac_z_batch<float, true>(const AcZArgs<float>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t launch_ac_z_batch<double, false>(const AcZArgs<double>*, const int*, int, int, int, int, size_t, int,
+                                    cudaStream_t);
+template cudaError_t batch_grid_ac_x<float, false>(int, int, size_t, int, int, int*);
+template cudaError_t batch_grid_ac_x<float, true>(int, int, size_t, int, int, int*);
+template cudaError_t batch_grid_ac_x<double, false>(int, int, size_t, int, int, int*);
+template cudaError_t batch_grid_ac_z<float, false>(int, int, size_t, int, int, int*);
+template cudaError_t batch_grid_ac_z<float, true>(int, int, size_t, int, int, int*);
+template cudaError_t batch_grid_ac_z<double, false>(int, int, size_t, int, int, int*);
+template cudaError_t launch_gather_batch<float>(const GatherJob<float>*, int, int64_t, cudaStream_t);
+template cudaError_t launch_gather_batch<double>(const GatherJob<double>*, int, int64_t, cudaStream_t);
 template cudaError_t launch_gather<float>(const float*, const int64_t*, int64_t, float*, int, const float*,
                                           const float*, const float*, cudaStream_t);
 template cudaError_t launch_gather<double>(const double*, const int64_t*, int64_t, double*, int, const double*,

@@ -2,7 +2,10 @@
 // sub-step A and the stress sub-step B.  Between steps the velocities are kept half a step ahead (staggered),
 // which merges the trailing half A of one step with the leading half A of the next; the state is brought back
 // to the integer time level (v_n = v_{n+1/2} + dt/2 b grad sigma_n) whenever velocities are read.
+#include <algorithm>
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "loss_host.h"
 
@@ -48,12 +51,8 @@ static T* rdelta(const Shot& s, int i, int j, double tau) {
   return (tau == s.d.dt && s.rdelta[0]) ? (T*)s.rdelta[3 * i + j] : nullptr;
 }
 
-template <typename T, bool K>
-static loss_status_t ac_x(loss_ctx* h, Shot& s, int do_B, double acoef, double src_amp) {
-  LineGeom g;
-  int logc, threads;
-  LOSS_TRY(line_geom(h, s, 2, s.sz, s.sy, &g, &logc, &threads, 3, 4, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_X],
-                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_X]));
+template <typename T>
+static AcXArgs<T> ac_x_args(loss_ctx* h, Shot& s, const LineGeom& g, int do_B, double acoef, double src_amp) {
   AcXArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[2], h->t32, h->t64};
@@ -86,16 +85,22 @@ static loss_status_t ac_x(loss_ctx* h, Shot& s, int do_B, double acoef, double s
     a.phiz = (T*)s.phi[0];
     a.dlt = rdelta<T>(s, 0, 0, acoef);
   }
+  return a;
+}
+
+template <typename T, bool K>
+static loss_status_t ac_x(loss_ctx* h, Shot& s, int do_B, double acoef, double src_amp) {
+  LineGeom g;
+  int logc, threads;
+  LOSS_TRY(line_geom(h, s, 2, s.sz, s.sy, &g, &logc, &threads, 3, 4, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_X],
+                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_X], h->tile_threads[LOSS_KERNEL_ACOUSTIC_X]));
+  const AcXArgs<T> a = ac_x_args<T>(h, s, g, do_B, acoef, src_amp);
   LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
   return cuda_check(h, launch_ac_x<T, K>(a, logc, threads, h->stream), "acoustic x kernel");
 }
 
-template <typename T, bool K>
-static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
-  LineGeom g;
-  int logc, threads;
-  LOSS_TRY(line_geom(h, s, 0, s.sz, s.sy, &g, &logc, &threads, 2, 0, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_Z],
-                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_Z]));
+template <typename T>
+static AcZArgs<T> ac_z_args(loss_ctx* h, Shot& s, const LineGeom& g, double acoef, int do_tmp) {
   AcZArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[0], h->t32, h->t64};
@@ -115,6 +120,16 @@ static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
     a.psiz = (T*)s.psi[0];
     a.dlt = rdelta<T>(s, 2, 2, acoef);
   }
+  return a;
+}
+
+template <typename T, bool K>
+static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
+  LineGeom g;
+  int logc, threads;
+  LOSS_TRY(line_geom(h, s, 0, s.sz, s.sy, &g, &logc, &threads, 2, 0, h->lines_per_block[LOSS_KERNEL_ACOUSTIC_Z],
+                     h->chunk_log2[LOSS_KERNEL_ACOUSTIC_Z], h->tile_threads[LOSS_KERNEL_ACOUSTIC_Z]));
+  const AcZArgs<T> a = ac_z_args<T>(h, s, g, acoef, do_tmp);
   LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_Z);
   return cuda_check(h, launch_ac_z<T, K>(a, logc, threads, h->stream), "acoustic z kernel");
 }
@@ -137,6 +152,13 @@ static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mo
   return LOSS_OK;
 }
 
+// Pressure-source increment of step n (applied in sub-step B at t_n + dt/2), or 0.
+static double pressure_amp(const Shot& s, int64_t n) {
+  if (!(s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE))) return 0.0;
+  const double dt = s.d.dt;
+  return dt * s.src_norm * ricker((double)n * dt + 0.5 * dt, s.src_f0, s.src_t0);
+}
+
 template <typename T, bool K>
 static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
   const double dt = s.d.dt;
@@ -147,10 +169,7 @@ static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
     s.staggered = true;
   }
   LOSS_TRY(gather_fields<T>(h, s, true, 0));  // v at t_{n+1/2}
-  double amp = 0.0;
-  if (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE))
-    amp = dt * s.src_norm * ricker((double)s.step * dt + 0.5 * dt, s.src_f0, s.src_t0);
-  LOSS_TRY((ac_x<T, K>(h, s, 1, dt, amp)));
+  LOSS_TRY((ac_x<T, K>(h, s, 1, dt, pressure_amp(s, s.step))));
   LOSS_TRY((ac_z<T, K>(h, s, dt, 1)));
   LOSS_TRY(gather_fields<T>(h, s, true, 1));   // (v_{n+1/2} + v_{n+3/2}) / 2 = v_{n+1}
   LOSS_TRY(gather_fields<T>(h, s, false, 0));  // sigma_{n+1}
@@ -180,7 +199,8 @@ static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A,
   LineGeom g;
   int logc, threads;
   const int kid = (k == 2) ? LOSS_KERNEL_ELASTIC_X : (k == 1 ? LOSS_KERNEL_ELASTIC_Y : LOSS_KERNEL_ELASTIC_Z);
-  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], h->chunk_log2[kid]));
+  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], h->chunk_log2[kid],
+                     h->tile_threads[kid]));
   ElArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[k], h->t32, h->t64};
@@ -278,6 +298,318 @@ static loss_status_t elastic3d_unstagger(loss_ctx* h, Shot& s) {
   LOSS_TRY((elastic_A<T, K>(h, s, -0.5 * s.d.dt, (double)s.step * s.d.dt)));
   s.staggered = false;
   return LOSS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------------------------
+// Batched schedule for handles of 2-D acoustic shots: each step is one persistent launch of the X kernel and one
+// of the Z kernel over the tiles of all shots, plus one launch per receiver phase and a clock tick.  Everything
+// that changes from step to step (source amplitude, trace row) is read from device memory, so a step's launches
+// have the same arguments every step: k steps are captured once in a CUDA graph and replayed.  Arithmetic is that
+// of the per-shot schedule, so both give the same fields and traces.
+
+bool batch_eligible(const loss_ctx* h) {
+  if (h->shots.empty()) return false;
+  if (!(h->graph_steps > 0 || (h->batched && h->shots.size() > 1))) return false;
+  const Shot& s0 = h->shots[0];
+  for (const Shot& s : h->shots)
+    if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2 || s.esize != s0.esize || s.kahan != s0.kahan) return false;
+  return true;
+}
+
+void batch_release(loss_ctx* h) {
+  if (h->batch.gexec) cudaGraphExecDestroy(h->batch.gexec);
+  h->batch.gexec = nullptr;
+  h->batch.gsig.clear();
+}
+
+void batch_destroy(loss_ctx* h) {
+  batch_release(h);
+  if (h->batch.cap_stream) cudaStreamDestroy(h->batch.cap_stream);
+  h->batch.cap_stream = nullptr;
+}
+
+// Per-step pressure amplitudes of steps 0 .. upto-1 in device memory (rebuilt when the source changed).
+static loss_status_t ensure_amp(loss_ctx* h, Shot& s, int64_t upto) {
+  const double sig[5] = {s.d.dt, s.src_norm, s.src_f0, s.src_t0, (double)(s.src_on ? s.src_kinds : 0u)};
+  bool same = s.amp_tab != nullptr;
+  for (int i = 0; i < 5 && same; ++i) same = sig[i] == s.amp_sig[i];
+  if (same && upto <= s.amp_cap) return LOSS_OK;
+  const int64_t cap = std::max<int64_t>(std::max<int64_t>(upto, same ? 2 * s.amp_cap : 0), 1024);
+  std::vector<double> a((size_t)cap);
+  for (int64_t n = 0; n < cap; ++n) a[n] = pressure_amp(s, n);
+  void* p = nullptr;
+  LOSS_TRY(dev_alloc(h, (size_t)cap * sizeof(double), &p));
+  LOSS_TRY(cuda_check(h, cudaMemcpyAsync(p, a.data(), (size_t)cap * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+                      "upload source amplitudes"));
+  LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  if (s.amp_tab) dev_free(h, s.amp_tab);
+  s.amp_tab = (double*)p;
+  s.amp_cap = cap;
+  for (int i = 0; i < 5; ++i) s.amp_sig[i] = sig[i];
+  return LOSS_OK;
+}
+
+// Geometry of every shot for one batched kernel, with one block size for all: the largest per-shot default
+// block (or the loss_set_tile target), each shot taking the widest bundle that fits in it.
+static loss_status_t batch_geoms(loss_ctx* h, int k, int kid, int nbuf, int nstage, std::vector<LineGeom>& gs,
+                                 int* logc, int* threads, size_t* smem) {
+  int target = h->tile_threads[kid];
+  if (target <= 0 && h->lines_per_block[kid] <= 0) {
+    for (Shot& s : h->shots) {
+      LineGeom g;
+      int lc, t;
+      LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &lc, &t, nbuf, nstage, 0, h->chunk_log2[kid]));
+      target = std::max(target, t);
+    }
+  }
+  if (target > kBatchThreads) target = kBatchThreads;
+  gs.resize(h->shots.size());
+  *logc = -1;
+  *threads = 0;
+  *smem = 0;
+  for (size_t i = 0; i < h->shots.size(); ++i) {
+    Shot& s = h->shots[i];
+    int lc, t;
+    LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &gs[i], &lc, &t, nbuf, nstage, h->lines_per_block[kid], h->chunk_log2[kid],
+                       target));
+    if (*logc >= 0 && lc != *logc) {
+      h->err = "batched shots need one chunk length";
+      return LOSS_E_UNSUPPORTED;
+    }
+    if (t > kBatchThreads) {
+      h->err = "batched launches hold at most " + std::to_string(kBatchThreads) + " threads per block";
+      return LOSS_E_UNSUPPORTED;
+    }
+    *logc = lc;
+    *threads = std::max(*threads, t);
+    *smem = std::max(*smem, smem_bytes(gs[i], nbuf, nstage, s.esize));
+  }
+  return LOSS_OK;
+}
+
+// Upload one device table when its contents changed (reallocating when it grew).
+static loss_status_t upload_table(loss_ctx* h, int which, const std::vector<unsigned char>& bytes, void** dptr) {
+  BatchState& B = h->batch;
+  if (bytes.size() > B.cap_bytes[which] || !*dptr) {
+    if (*dptr) dev_free(h, *dptr);
+    *dptr = nullptr;
+    LOSS_TRY(dev_alloc(h, std::max<size_t>(bytes.size(), 64), dptr));
+    B.cap_bytes[which] = std::max<size_t>(bytes.size(), 64);
+    B.host[which].clear();
+  }
+  if (bytes == B.host[which]) return LOSS_OK;
+  if (!bytes.empty())
+    LOSS_TRY(cuda_check(h, cudaMemcpyAsync(*dptr, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, h->stream),
+                        "upload batch tables"));
+  LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  B.host[which] = bytes;
+  return LOSS_OK;
+}
+
+template <class V>
+static std::vector<unsigned char> as_bytes(const std::vector<V>& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  return std::vector<unsigned char>(p, p + v.size() * sizeof(V));
+}
+
+template <typename T, bool K>
+static loss_status_t batch_launch_step(loss_ctx* h) {
+  BatchState& B = h->batch;
+  const int S = (int)h->shots.size();
+  const GatherJob<T>* jobs = (const GatherJob<T>*)B.jobs;
+  if (B.npre) {
+    LaunchScope ls(h, LOSS_KERNEL_GATHER);
+    LOSS_TRY(cuda_check(h, launch_gather_batch<T>(jobs, B.npre, B.pre_max, h->stream), "batched receiver gather"));
+  }
+  {
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
+    LOSS_TRY(cuda_check(h, launch_ac_x_batch<T, K>((const AcXArgs<T>*)B.xtab, B.tile0, S, B.xtiles, B.xlogc,
+                                                   B.xthreads, B.xsmem, B.xgrid, h->stream),
+                        "batched acoustic x kernel"));
+  }
+  {
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_Z);
+    LOSS_TRY(cuda_check(h, launch_ac_z_batch<T, K>((const AcZArgs<T>*)B.ztab, B.tile0 + S + 1, S, B.ztiles, B.zlogc,
+                                                   B.zthreads, B.zsmem, B.zgrid, h->stream),
+                        "batched acoustic z kernel"));
+  }
+  if (B.npost) {
+    LaunchScope ls(h, LOSS_KERNEL_GATHER);
+    LOSS_TRY(cuda_check(h, launch_gather_batch<T>(jobs + B.npre, B.npost, B.post_max, h->stream),
+                        "batched receiver gather"));
+  }
+  LaunchScope ls(h, LOSS_KERNEL_CLOCK);
+  return cuda_check(h, launch_tick(B.clk, S, h->stream), "clock tick");
+}
+
+template <typename T, bool K>
+static loss_status_t capture_graph(loss_ctx* h, int64_t k) {
+  BatchState& B = h->batch;
+  batch_release(h);
+  int64_t snap[LOSS_NUM_KERNELS];
+  for (int i = 0; i < LOSS_NUM_KERNELS; ++i) snap[i] = h->launches[i];
+  if (!B.cap_stream)
+    LOSS_TRY(cuda_check(h, cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking), "create capture stream"));
+  // Capturing records the launches without running them, so the captured stream needs no ordering with the
+  // handle's stream; the replays are issued on the handle's stream.
+  cudaStream_t own = h->stream;
+  LOSS_TRY(cuda_check(h, cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal),
+                      "begin graph capture"));
+  h->stream = B.cap_stream;
+  h->capturing = true;
+  loss_status_t st = LOSS_OK;
+  for (int64_t i = 0; i < k && st == LOSS_OK; ++i) st = batch_launch_step<T, K>(h);
+  h->capturing = false;
+  h->stream = own;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(B.cap_stream, &graph);
+  for (int i = 0; i < LOSS_NUM_KERNELS; ++i) {
+    B.graph_launches[i] = h->launches[i] - snap[i];
+    h->launches[i] = snap[i];
+  }
+  if (st != LOSS_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != LOSS_OK ? st : cuda_check(h, e, "end graph capture");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&B.gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    B.gexec = nullptr;
+    return cuda_check(h, ei, "instantiate graph");
+  }
+  B.graph_k = k;
+  return LOSS_OK;
+}
+
+template <typename T, bool K>
+static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
+  BatchState& B = h->batch;
+  const int S = (int)h->shots.size();
+  // per-shot preparation: receiver corrections, staggered start, source amplitudes
+  for (Shot& s : h->shots) {
+    LOSS_TRY(ensure_rdelta(h, s));
+    if (!s.staggered) {
+      LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * s.d.dt, 0.0)));
+      LOSS_TRY((ac_z<T, K>(h, s, 0.5 * s.d.dt, 1)));
+      s.staggered = true;
+    }
+    LOSS_TRY(ensure_amp(h, s, s.step + n));
+  }
+  // launch shapes and descriptors
+  std::vector<LineGeom> gx, gz;
+  LOSS_TRY(batch_geoms(h, 2, LOSS_KERNEL_ACOUSTIC_X, 3, 4, gx, &B.xlogc, &B.xthreads, &B.xsmem));
+  LOSS_TRY(batch_geoms(h, 0, LOSS_KERNEL_ACOUSTIC_Z, 2, 0, gz, &B.zlogc, &B.zthreads, &B.zsmem));
+  if (B.clk_cap < S) {
+    if (B.clk) dev_free(h, B.clk);
+    void* p = nullptr;
+    LOSS_TRY(dev_alloc(h, (size_t)S * sizeof(StepClock), &p));
+    B.clk = (StepClock*)p;
+    B.clk_cap = S;
+    B.clk_host.clear();
+  }
+  std::vector<AcXArgs<T>> xa(S);
+  std::vector<AcZArgs<T>> za(S);
+  std::vector<int> t0(2 * (S + 1), 0);
+  std::vector<GatherJob<T>> pre, post;
+  int64_t pre_max = 0, post_max = 0;
+  for (int i = 0; i < S; ++i) {
+    Shot& s = h->shots[i];
+    xa[i] = ac_x_args<T>(h, s, gx[i], 1, s.d.dt, 0.0);
+    xa[i].src.on = (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE)) ? 1 : 0;
+    xa[i].src.amp_tab = s.amp_tab;
+    xa[i].src.clk = B.clk + i;
+    za[i] = ac_z_args<T>(h, s, gz[i], s.d.dt, 1);
+    t0[i + 1] = t0[i] + gx[i].nbundles;
+    t0[S + 1 + i + 1] = t0[S + 1 + i] + gz[i].nbundles;
+    for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {
+      if (s.n_rcv == 0) break;
+      const int64_t off = s.rcv_offsets[f], cnt = s.rcv_offsets[f + 1] - off;
+      if (cnt == 0) continue;
+      GatherJob<T> j{};
+      j.f = (const T*)s.field[f];
+      j.idx = s.rcv_idx + off;
+      j.cnt = cnt;
+      j.trace = (T*)s.traces;
+      j.n_rcv = s.n_rcv;
+      j.off = off;
+      j.clk = B.clk + i;
+      if (is_velocity(f)) {
+        j.mode = 0;
+        pre.push_back(j);
+        pre_max = std::max(pre_max, cnt);
+        j.mode = 1;
+        if (s.rdelta[0])
+          for (int d = 0; d < 3; ++d) j.d[d] = (const T*)s.rdelta[3 * f + d];
+      } else {
+        j.mode = 0;
+      }
+      post.push_back(j);
+      post_max = std::max(post_max, cnt);
+    }
+  }
+  B.xtiles = t0[S];
+  B.ztiles = t0[2 * S + 1];
+  B.npre = (int)pre.size();
+  B.npost = (int)post.size();
+  B.pre_max = pre_max;
+  B.post_max = post_max;
+  std::vector<GatherJob<T>> jobs = pre;
+  jobs.insert(jobs.end(), post.begin(), post.end());
+  LOSS_TRY(upload_table(h, 0, as_bytes(xa), &B.xtab));
+  LOSS_TRY(upload_table(h, 1, as_bytes(za), &B.ztab));
+  void* t0p = B.tile0;
+  LOSS_TRY(upload_table(h, 2, as_bytes(t0), &t0p));
+  B.tile0 = (int*)t0p;
+  LOSS_TRY(upload_table(h, 3, as_bytes(jobs), &B.jobs));
+  // device clocks: set from the host counters unless they already hold them
+  std::vector<StepClock> ck(S);
+  for (int i = 0; i < S; ++i)
+    ck[i] = StepClock{h->shots[i].step, h->shots[i].rcv_steps, h->shots[i].n_rcv ? 1 : 0, 0};
+  std::vector<unsigned char> ckb = as_bytes(ck);
+  if (ckb != B.clk_host) {
+    LOSS_TRY(cuda_check(h, cudaMemcpyAsync(B.clk, ckb.data(), ckb.size(), cudaMemcpyHostToDevice, h->stream),
+                        "upload clocks"));
+    LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  }
+  LOSS_TRY(cuda_check(h, batch_grid_ac_x<T, K>(B.xlogc, B.xthreads, B.xsmem, B.xtiles, h->num_sms, &B.xgrid),
+                      "batched x kernel shape"));
+  LOSS_TRY(cuda_check(h, batch_grid_ac_z<T, K>(B.zlogc, B.zthreads, B.zsmem, B.ztiles, h->num_sms, &B.zgrid),
+                      "batched z kernel shape"));
+  // launches
+  int64_t done = 0;
+  const int64_t k = h->graph_steps;
+  if (k > 0 && n >= k) {
+    const std::vector<int64_t> sig = {B.xthreads, (int64_t)B.xsmem, B.xlogc, B.xtiles, B.xgrid, B.zthreads,
+                                      (int64_t)B.zsmem, B.zlogc, B.ztiles, B.zgrid, B.npre, B.npost, B.pre_max,
+                                      B.post_max, (int64_t)(intptr_t)B.xtab, (int64_t)(intptr_t)B.ztab,
+                                      (int64_t)(intptr_t)B.tile0, (int64_t)(intptr_t)B.jobs,
+                                      (int64_t)(intptr_t)B.clk, S, (int64_t)sizeof(T), K ? 1 : 0, k};
+    if (!B.gexec || sig != B.gsig) {
+      LOSS_TRY((capture_graph<T, K>(h, k)));
+      B.gsig = sig;
+    }
+    for (; n - done >= k; done += k) {
+      LOSS_TRY(cuda_check(h, cudaGraphLaunch(B.gexec, h->stream), "graph launch"));
+      for (int i = 0; i < LOSS_NUM_KERNELS; ++i) h->launches[i] += B.graph_launches[i];
+    }
+  }
+  for (; done < n; ++done) LOSS_TRY((batch_launch_step<T, K>(h)));
+  for (int i = 0; i < S; ++i) {
+    Shot& s = h->shots[i];
+    s.step += n;
+    if (s.n_rcv) s.rcv_steps += n;
+    ck[i] = StepClock{s.step, s.rcv_steps, s.n_rcv ? 1 : 0, 0};
+  }
+  B.clk_host = as_bytes(ck);
+  return LOSS_OK;
+}
+
+loss_status_t step_batched(loss_ctx* h, int64_t n) {
+  if (n <= 0) return LOSS_OK;
+  const Shot& s = h->shots[0];
+  if (s.esize == 8) return step_batched_t<double, false>(h, n);
+  if (s.kahan) return step_batched_t<float, true>(h, n);
+  return step_batched_t<float, false>(h, n);
 }
 
 loss_status_t step_shot(loss_ctx* h, Shot& s) {

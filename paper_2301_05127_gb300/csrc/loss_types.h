@@ -53,11 +53,42 @@ struct DerivArgs {
   int lines_per_outer;  // S flavour: lines per outer index in the phi_out ordering (= nx1)
 };
 
+// Largest block of the persistent batched kernels.
+constexpr int kBatchThreads = 512;
+
+// Device-side step counters of one shot, used by launches whose arguments do not change from step to step
+// (persistent batched launches and captured CUDA graphs): step = index n of the step being taken, row = trace row
+// the step's receiver values go to; both advance once per step (row by row_inc, 1 when the shot records).
+struct StepClock {
+  int64_t step;
+  int64_t row;
+  int64_t row_inc;
+  int64_t pad;
+};
+
 struct SourceArgs {
   int on;
   int zs, ys, xs;    // centre
   double amp;        // dt * amp * f_r(t) / (sum of profile * cell volume), or 0
   double g[25];      // exp(-o^2 / 8), o = -12..12
+  // When amp_tab is set, the amplitude of step n is amp_tab[clk->step] (same host-computed values as amp).
+  const double* amp_tab;
+  const StepClock* clk;
+};
+
+// One receiver gather of a batched launch: out row = trace + clk->row * n_rcv + off (see k_gather for modes).
+template <typename T>
+struct GatherJob {
+  const T* f;
+  const int64_t* idx;
+  int64_t cnt;
+  T* trace;
+  int64_t n_rcv;
+  int64_t off;
+  const T* d[3];
+  const StepClock* clk;
+  int mode;
+  int pad;
 };
 
 // Exponential-flow coefficients of the ADE-PML along one axis for one step length tau (paper Sec. 3.3):
