@@ -16,4 +16,4 @@ spline   1-D cubic-B-spline collocation, PMBC weights and closures, local solves
 wave     acoustic and elastic velocity-stress steppers, Ricker source, receivers, energy (Sec. 2, 3.3, 4)
 adjoint  discrete adjoint of the stepper and the misfit gradient with respect to vp, vs, rho
 """
-from . import spline, wave  # noqa: F401
+from . import adjoint, spline, wave  # noqa: F401
