@@ -170,6 +170,29 @@ loss_status_t loss_derivative(loss_handle_t handle, int32_t shot, int32_t axis, 
  * shape [lines][p + 1] in double, lines ordered as the dense array with `axis` removed. */
 loss_status_t loss_pmbc_phi(loss_handle_t handle, int32_t shot, int32_t axis, const void* f, double* phi, int32_t mem);
 
+/* Transposed LOSS first derivative along `axis`: out = D^T g, with D the operator of loss_derivative (same
+ * arrays, layouts and memory rules; out is overwritten).  Per line D = (3/h) P with P f = e the compact solve
+ * of every patch closed by the PMBC junction values (Sec. 3.2); P^T runs the same symmetric tridiagonal solve
+ * on the patch interiors (zero junction values) and scatters the junction adjoints back with the PMBC weights.
+ * The paper has no counterpart: it is the building block of loss_gradient.  Errors as loss_derivative. */
+loss_status_t loss_derivative_adjoint(loss_handle_t handle, int32_t shot, int32_t axis, const void* g, void* out,
+                                      int32_t mem);
+
+/* Seismogram misfit J = 1/2 sum_{n < n_steps} sum_r (trace_{n,r} - d_obs_{n,r})^2 of shot `shot` and its gradient
+ * with respect to the model grids, by the discrete adjoint of the time step the library takes (the paper has
+ * no adjoint).  The shot is reset to rest (every field, compensation term and PML memory variable zero, step 0,
+ * recorded traces dropped), advanced n_steps steps with its model, source, absorbing layers and receivers, and
+ * then the adjoint runs backwards, recomputing the forward states segment by segment from checkpoints taken
+ * every checkpoint_every steps (0 = ceil(sqrt(n_steps))); device memory for about n_steps / C + C states.
+ * d_obs: [n_steps][n_receivers] doubles in the order of loss_record.  g_vp, g_vs (elastic only; NULL allowed for
+ * acoustic grids), g_rho: dense arrays of the grid shape, doubles, written.  mem says where d_obs and the
+ * gradients live.  The gradient is dJ/d(model) with the time step, the absorbing profile (whose damping uses
+ * the largest vp) and the source fixed.  Afterwards the shot is at step n_steps with its traces recorded.
+ * Built for 2-D acoustic and 3-D elastic grids with stress-type sources; LOSS_E_UNSUPPORTED for a body force,
+ * LOSS_E_STATE without a model or receivers, LOSS_E_ARG for bad arguments. */
+loss_status_t loss_gradient(loss_handle_t handle, int32_t shot, const double* d_obs, int32_t checkpoint_every,
+                            int64_t n_steps, double* misfit, double* g_vp, double* g_vs, double* g_rho, int32_t mem);
+
 /* Serialise / restore the full time-stepping state of every shot (fields, compensation terms, step
  * counters) at the current integer time level.  loss_get_state with blob = NULL returns the size. */
 loss_status_t loss_get_state(loss_handle_t handle, void* blob, size_t* bytes);
@@ -188,6 +211,7 @@ enum {
   LOSS_KERNEL_ELASTIC_Y = 5,  /* 3-D elastic passes on y lines */
   LOSS_KERNEL_ELASTIC_Z = 6,  /* 3-D elastic passes on z lines */
   LOSS_KERNEL_CLOCK = 7,      /* batched schedule: end-of-step advance of the device step counters */
+  LOSS_KERNEL_ADJOINT = 8,    /* adjoint terms and the transposed derivative (loss_gradient, loss_derivative_adjoint) */
   LOSS_NUM_KERNELS = 16
 };
 

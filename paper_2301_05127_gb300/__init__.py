@@ -70,6 +70,8 @@ _PROTOS = {
     "loss_record": (_I32, [_H, _I32, _P, _I32]),
     "loss_derivative": (_I32, [_H, _I32, _I32, _P, _P, _P, _I32]),
     "loss_pmbc_phi": (_I32, [_H, _I32, _I32, _P, _P, _I32]),
+    "loss_derivative_adjoint": (_I32, [_H, _I32, _I32, _P, _P, _I32]),
+    "loss_gradient": (_I32, [_H, _I32, _P, _I32, _I64, ctypes.POINTER(_D), _P, _P, _P, _I32]),
     "loss_get_state": (_I32, [_H, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "loss_set_state": (_I32, [_H, _P, ctypes.c_size_t]),
     "loss_get_step": (_I32, [_H, _I32, ctypes.POINTER(_I64)]),
@@ -83,7 +85,7 @@ _PROTOS = {
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
 KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
-           "elastic_z": 6, "clock": 7}
+           "elastic_z": 6, "clock": 7, "adjoint": 8}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -225,6 +227,15 @@ class Grid:
 
     # -- C ABI wrappers -----------------------------------------------------------------------------------------
     def set_model(self, shot, vp, vs, rho):
+        """vp, vs (None for acoustic grids), rho: float64 numpy arrays or torch tensors of the grid shape."""
+        if not isinstance(vp, np.ndarray):
+            import torch
+            cvt = lambda a: None if a is None else a.detach().to(torch.float64).contiguous()  # noqa: E731
+            vp, vs, rho = cvt(vp), cvt(vs), cvt(rho)
+            mem = LOSS_MEM_DEVICE if vp.is_cuda else LOSS_MEM_HOST
+            _check(lib().loss_set_model(self.h, shot, vp.data_ptr(), None if vs is None else vs.data_ptr(),
+                                        rho.data_ptr(), mem), self.h)
+            return
         vp = np.ascontiguousarray(vp, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         vsa = None if vs is None else np.ascontiguousarray(vs, dtype=np.float64)
@@ -290,6 +301,41 @@ class Grid:
         if mem == LOSS_MEM_DEVICE:
             self.sync()
         return (d1, d2) if second else d1
+
+    def derivative_adjoint(self, shot, axis, g):
+        """D^T g along ``axis`` (transpose of ``derivative``); numpy or torch cuda, like ``derivative``."""
+        if isinstance(g, np.ndarray):
+            g = np.ascontiguousarray(g, dtype=self.dtype)
+            out = np.empty_like(g)
+        else:
+            out = g.new_empty(g.shape)
+        gp, mem = _ptr_and_mem(g)
+        _check(lib().loss_derivative_adjoint(self.h, shot, axis, gp, _ptr_and_mem(out)[0], mem), self.h)
+        if mem == LOSS_MEM_DEVICE:
+            self.sync()
+        return out
+
+    def gradient(self, shot, d_obs, n_steps, checkpoint_every=0):
+        """Misfit 1/2 ||traces - d_obs||^2 over n_steps steps from rest and its gradient with respect to vp, vs,
+        rho (loss_gradient).  d_obs: [n_steps, n_receivers] float64 (numpy, or torch on the device).  Returns
+        (J, {"vp", "vs", "rho"}) with arrays of the grid shape (numpy, or torch tensors on d_obs's device)."""
+        shape = self.shape(shot)
+        elastic = self.descs[shot].physics == LOSS_ELASTIC
+        J = _D()
+        if isinstance(d_obs, np.ndarray):
+            d_obs = np.ascontiguousarray(d_obs, dtype=np.float64)
+            g = {k: np.zeros(shape) for k in ("vp", "vs", "rho")}
+        else:
+            import torch
+            d_obs = d_obs.detach().to(torch.float64).contiguous()
+            g = {k: torch.zeros(shape, dtype=torch.float64, device=d_obs.device) for k in ("vp", "vs", "rho")}
+        dp, mem = _ptr_and_mem(d_obs)
+        _check(lib().loss_gradient(self.h, shot, dp, int(checkpoint_every), int(n_steps), ctypes.byref(J),
+                                   _ptr_and_mem(g["vp"])[0], _ptr_and_mem(g["vs"])[0] if elastic else None,
+                                   _ptr_and_mem(g["rho"])[0], mem), self.h)
+        if not elastic:
+            g["vs"] = None
+        return J.value, g
 
     def pmbc_phi(self, shot, axis, f):
         f = np.ascontiguousarray(f, dtype=self.dtype)

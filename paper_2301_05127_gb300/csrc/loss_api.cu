@@ -694,6 +694,10 @@ loss_status_t loss_set_model(loss_handle_t h, int32_t shot, const double* vp, co
       md[1][i] = 1.0 / r;              // b
     }
   }
+  s->h_vp.assign(pvp, pvp + N);
+  s->h_rho.assign(prho, prho + N);
+  if (el) s->h_vs.assign(pvs, pvs + N);
+  else s->h_vs.clear();
   s->vmax = 0.0;
   for (int64_t i = 0; i < N; ++i) s->vmax = std::max(s->vmax, std::fabs(pvp[i]));
   s->b_const = true;
@@ -949,6 +953,22 @@ loss_status_t loss_derivative(loss_handle_t h, int32_t shot, int32_t axis, const
   if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
   if (!f || !d1 || (mem != LOSS_MEM_HOST && mem != LOSS_MEM_DEVICE)) return fail(h, LOSS_E_ARG, "bad buffers");
   return run_derivative(h, *s, axis_slot(*s, axis), f, d1, d2, nullptr, mem);
+}
+
+loss_status_t loss_derivative_adjoint(loss_handle_t h, int32_t shot, int32_t axis, const void* g, void* out,
+                                      int32_t mem) {
+  Shot* s;
+  LOSS_TRY(get_shot(h, shot, &s));
+  if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
+  if (!g || !out || (mem != LOSS_MEM_HOST && mem != LOSS_MEM_DEVICE)) return fail(h, LOSS_E_ARG, "bad buffers");
+  return run_derivative_adjoint(h, *s, axis_slot(*s, axis), g, out, mem);
+}
+
+loss_status_t loss_gradient(loss_handle_t h, int32_t shot, const double* d_obs, int32_t checkpoint_every,
+                            int64_t n_steps, double* misfit, double* g_vp, double* g_vs, double* g_rho, int32_t mem) {
+  Shot* s;
+  LOSS_TRY(get_shot(h, shot, &s));
+  return run_gradient(h, *s, d_obs, checkpoint_every, n_steps, misfit, g_vp, g_vs, g_rho, mem);
 }
 
 loss_status_t loss_pmbc_phi(loss_handle_t h, int32_t shot, int32_t axis, const void* f, double* phi, int32_t mem) {

@@ -62,6 +62,14 @@ struct Shot {
   // time stepping
   int64_t step = 0;
   bool staggered = false;  // velocities hold v at t_step + dt/2 instead of t_step
+  // model as given to loss_set_model (dense, FP64), for the chain rule of the misfit gradient
+  std::vector<double> h_vp, h_vs, h_rho;
+  // adjoint workspace (loss_gradient): adjoint fields, adjoint PML memory variables (same slots as psi/phi or
+  // pmem), velocity residual arrays, FP64 gradients of (lambda or kappa, mu, b)
+  void* lam[LOSS_NUM_FIELDS] = {};
+  void* lam_mem[18] = {};
+  void* rv[3] = {};
+  double* grad[3] = {};
   // per-step source amplitudes for launches that read them from the device (batched / graph schedule)
   double* amp_tab = nullptr;
   int64_t amp_cap = 0;
@@ -141,6 +149,10 @@ loss_status_t validate(const loss_grid_desc_t& d, std::string* why);
 bool is_velocity(int f);
 loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows);
 loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d1, void* d2, double* phi, int mem);
+// loss_adjoint.cu
+loss_status_t run_derivative_adjoint(loss_ctx* h, Shot& s, int k, const void* g, void* out, int mem);
+loss_status_t run_gradient(loss_ctx* h, Shot& s, const double* d_obs, int32_t checkpoint_every, int64_t n_steps,
+                           double* misfit, double* g_vp, double* g_vs, double* g_rho, int32_t mem);
 std::vector<double> pmbc_weights_scaled(int n, int p, int n_nb);
 void thomas_tables(std::vector<double>& t64, std::vector<float>& t32);
 
@@ -165,6 +177,7 @@ struct LaunchScope {
 // loss_step.cu
 loss_status_t step_shot(loss_ctx* h, Shot& s);
 loss_status_t unstagger(loss_ctx* h, Shot& s);
+loss_status_t stagger_shot(loss_ctx* h, Shot& s);
 bool batch_eligible(const loss_ctx* h);
 loss_status_t step_batched(loss_ctx* h, int64_t n_steps);
 void batch_release(loss_ctx* h);
@@ -196,5 +209,10 @@ cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshot
 template <typename T>
 cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
 cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj(const AdjArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_inject(const InjectJob<T>* jobs, int njobs, int64_t max_cnt, int64_t row, int64_t row_stride,
+                          int phase, cudaStream_t st);
 
 }  // namespace lossk

@@ -122,6 +122,11 @@ struct RhsD1 {
   template <typename T>
   __device__ __forceinline__ T operator()(T fm1, T f0, T fp1) const { return fp1 - fm1; }
 };
+// Right-hand side q_i = f_i (the symmetric tridiagonal solve of the transposed derivative).
+struct RhsId {
+  template <typename T>
+  __device__ __forceinline__ T operator()(T fm1, T f0, T fp1) const { return f0; }
+};
 // Second-derivative right-hand side q_i = f_{i+1} - 2 f_i + f_{i-1}.
 struct RhsD2 {
   template <typename T>
@@ -319,6 +324,13 @@ __device__ void solve_bundle(const T* __restrict__ f, T* __restrict__ out, T* __
   }
   __syncthreads();
 }
+
+// Zero boundary values (transposed derivative: the junction unknowns are not solved for).
+template <typename T>
+struct BndZero {
+  __device__ __forceinline__ T left(int, int) const { return T(0); }
+  __device__ __forceinline__ T right(int, int) const { return T(0); }
+};
 
 // Boundary values e_0 = phi_l, e_M = phi_{l+1} (first derivative).
 template <typename T>

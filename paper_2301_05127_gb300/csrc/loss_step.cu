@@ -627,6 +627,35 @@ loss_status_t step_shot(loss_ctx* h, Shot& s) {
   return LOSS_E_UNSUPPORTED;
 }
 
+// The staggered start (half velocity sub-step) on its own.
+loss_status_t stagger_shot(loss_ctx* h, Shot& s) {
+  if (s.staggered) return LOSS_OK;
+  LOSS_TRY(ensure_rdelta(h, s));
+  const double dt = s.d.dt;
+  if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {
+    if (s.esize == 8) {
+      LOSS_TRY((ac_x<double, false>(h, s, 0, 0.5 * dt, 0.0)));
+      LOSS_TRY((ac_z<double, false>(h, s, 0.5 * dt, 1)));
+    } else if (s.kahan) {
+      LOSS_TRY((ac_x<float, true>(h, s, 0, 0.5 * dt, 0.0)));
+      LOSS_TRY((ac_z<float, true>(h, s, 0.5 * dt, 1)));
+    } else {
+      LOSS_TRY((ac_x<float, false>(h, s, 0, 0.5 * dt, 0.0)));
+      LOSS_TRY((ac_z<float, false>(h, s, 0.5 * dt, 1)));
+    }
+  } else if (s.d.physics == LOSS_ELASTIC) {
+    const double tn = (double)s.step * dt;
+    if (s.esize == 8) LOSS_TRY((elastic_A<double, false>(h, s, 0.5 * dt, tn)));
+    else if (s.kahan) LOSS_TRY((elastic_A<float, true>(h, s, 0.5 * dt, tn)));
+    else LOSS_TRY((elastic_A<float, false>(h, s, 0.5 * dt, tn)));
+  } else {
+    h->err = "time stepping of this physics/dimension is not built";
+    return LOSS_E_UNSUPPORTED;
+  }
+  s.staggered = true;
+  return LOSS_OK;
+}
+
 loss_status_t unstagger(loss_ctx* h, Shot& s) {
   if (!s.staggered) return LOSS_OK;
   if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {

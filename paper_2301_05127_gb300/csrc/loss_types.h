@@ -192,4 +192,45 @@ struct ElArgs {
   int src_explosive, src_shear;
 };
 
+// One term of the adjoint of the time step (see loss_kernels_adjoint.cu).  A term is a forward update
+// "field += c * Z" with Z = sgn * X and X the (PML) integral over tau of minus the derivative along the line axis
+// of the forward field ffwd; the kernel adds D^T gbar to `out`, where gbar is the adjoint of that derivative,
+// updates the adjoint memory variable and accumulates the model gradients.
+template <typename T>
+struct AdjArgs {
+  LineGeom g;
+  Tables tb;
+  T s3h, minf;
+  double s3hd;       // 3 / h in double
+  int mode;          // 0: out += D^T in3 only; 1: velocity-sub-step term; 2: stress-sub-step term
+  T sgn;             // +1 (acoustic: field += c X) or -1 (elastic: field += c (-X))
+  T tau;             // sub-step length
+  const T* ffwd;     // forward field differentiated along the line axis (modes 1, 2)
+  const T* memf;     // forward memory variable of the term before the sub-step (in layers), or null
+  T* memb;           // adjoint memory variable of the term (in / out), or null
+  int pml;
+  PmlAxis<T> pa;     // tables for tau and, for the receiver terms of mode 1, tau / 2 (tabh)
+  const T* in[3];    // adjoint inputs weighted by c1 (summed), or null
+  const T* in3;      // adjoint input weighted by c2
+  const T* rv;       // mode 1: trace residual at velocity receivers (zero elsewhere), or null
+  const T* c1;       // coefficient arrays, or null for the scalars c1s / c2s
+  const T* c2;
+  T c1s, c2s, cw2;   // c2 = cw2 * (c2 array or c2s)
+  double* g1;        // gradient of the c1 parameter: += Z * sum(in), or null
+  double* g2;        // gradient of the c2 parameter: += Z * gw2 * in3 + Zh * rv, or null
+  T gw2;
+  T* out;
+};
+
+// Receiver residual injection of one adjoint step.  phase 0: stress fields lam[idx] += r, velocity residual
+// arrays rv[idx] += r; phase 1: velocity fields lam[idx] += r and rv[idx] = 0.
+template <typename T>
+struct InjectJob {
+  T* lam;
+  T* rv;             // velocity receivers only, else null
+  const int64_t* idx;
+  const double* r;   // residual of this field's receivers for the step
+  int64_t cnt;
+};
+
 }  // namespace lossk

@@ -9,6 +9,9 @@ from .workloads import (  # noqa: F401
     Workload,
     WORKLOADS,
     acoustic2d_small,
+    acoustic2d_gradient_case,
+    elastic3d_gradient_case,
+    mean_model,
     acoustic2d_layered,
     elastic3d_homogeneous,
     elastic3d_heterogeneous,

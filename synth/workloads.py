@@ -249,6 +249,43 @@ def scaled(w: Workload, n: int, p: int, steps: int, n_nb: Optional[int] = None,
         pml_width=w.pml_width if pml_width is None else pml_width)
 
 
+def acoustic2d_gradient_case(n: int = 24, p: int = 2, n_nb: int = 6, steps: int = 40, pml_width: int = 5,
+                              precision: str = "fp64"):
+    """Small misfit-gradient case: (n+1)^2 points, smooth random vp (2000 m/s +- 5 %) and rho (1000 +- 5 %),
+    seeds 11 and 12, a 60 Hz pressure source at the centre, pressure and velocity receivers on the rows z = 2
+    (inside the absorbing layer) and z = n - 4.  Returns (workload, (vp, None, rho))."""
+    w = acoustic2d_small(n=n, p=p, n_nb=n_nb, steps=steps, pml_width=pml_width)
+    shape = w.shape
+    vp = 2000.0 * (1 + 0.05 * random_field(shape, 11, 2.0))
+    rho = 1000.0 * (1 + 0.05 * random_field(shape, 12, 2.0))
+    rows = np.concatenate([2 * (n + 1) + np.arange(n + 1), (n - 4) * (n + 1) + np.arange(n + 1)]).astype(np.int64)
+    w = dataclasses.replace(w, f0=60.0, t0=1.2 / 60.0, dt=0.4 * 10.0 / vp.max(), precision=precision,
+                            receivers={"sigma": rows, "v1": rows, "v3": rows}, model_fn=lambda: (vp, None, rho))
+    return w, (vp, None, rho)
+
+
+def elastic3d_gradient_case(n: int = 12, p: int = 2, n_nb: int = 4, steps: int = 24, pml_width: int = 3,
+                            src_kinds=("explosive", "shear_xz"), precision: str = "fp64"):
+    """Small misfit-gradient case: (n+1)^3 points, smooth random vp (3000 +- 5 %), vs (1730 +- 5 %), rho
+    (2000 +- 5 %), seeds 21-23, an 80 Hz source at the centre, v1..v3 and s33 receivers on the plane z = 1.
+    Returns (workload, (vp, vs, rho))."""
+    w = elastic3d_homogeneous(n=n, p=p, n_nb=n_nb, steps=steps, pml_width=pml_width)
+    shape = w.shape
+    vp = 3000.0 * (1 + 0.05 * random_field(shape, 21, 2.0))
+    vs = 1730.0 * (1 + 0.05 * random_field(shape, 22, 2.0))
+    rho = 2000.0 * (1 + 0.05 * random_field(shape, 23, 2.0))
+    plane = ((n + 1) ** 2 + np.arange((n + 1) ** 2)).astype(np.int64)
+    w = dataclasses.replace(w, f0=80.0, t0=1.2 / 80.0, dt=0.4 * 10.0 / vp.max(), src_kinds=tuple(src_kinds),
+                            precision=precision, receivers={"v1": plane, "v2": plane, "v3": plane, "s33": plane},
+                            model_fn=lambda: (vp, vs, rho))
+    return w, (vp, vs, rho)
+
+
+def mean_model(model):
+    """Homogeneous model with the means of ``model`` (the data of the gradient cases come from it)."""
+    return tuple(None if a is None else np.full(a.shape, float(a.mean())) for a in model)
+
+
 WORKLOADS = {
     "acoustic2d_small": acoustic2d_small,
     "acoustic2d_layered": acoustic2d_layered,

@@ -1,0 +1,176 @@
+"""GPU tests of the discrete adjoint through the C ABI: the transposed derivative against the oracle's explicit
+transpose and the dot-product identity, the misfit gradient against the oracle's adjoint (FP64 and FP32), its
+independence of the checkpoint interval, the torch.autograd binding, a finite-difference check on the GPU, and
+the heterogeneous 3-D elastic geometry (193^3 points, 4 x 4 x 4 patches)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle.wave import Operator
+from synth import (acoustic2d_gradient_case, elastic3d_gradient_case, elastic3d_heterogeneous, mean_model,
+                   random_field)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as ge
+
+    ge.build()
+    import paper_2301_05127_gb300 as p
+
+    return p
+
+
+def _grid(pkg, dim, n, p, h, n_nb, prec):
+    d = pkg.make_desc(dim, pkg.LOSS_ACOUSTIC, pkg.PRECISIONS[prec], n_nb, n, p, h, 1e-3)
+    return pkg.Grid([d])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", [
+    (2, (40, 36), (4, 3), (10.0, 7.0), 8),     # several patches, different n per axis
+    (2, (12, 30), (1, 2), (1.0, 2.0), 12),     # one patch; halo width equal to the patch length
+    (3, (16, 20, 24), (2, 2, 4), (1.0, 1.5, 2.0), 6),
+])
+def test_derivative_adjoint_is_the_transpose(pkg, prec, case):
+    dim, n, p, h, n_nb = case
+    g = _grid(pkg, dim, n, p, h, n_nb, prec)
+    shape = tuple(k + 1 for k in n)
+    rng = np.random.default_rng(7)
+    gin = rng.standard_normal(shape)
+    f = rng.standard_normal(shape)
+    op = Operator(n, p, h, n_nb)
+    tol = 1e-12 if prec == "fp64" else 3e-6
+    for axis in range(dim):
+        out = g.derivative_adjoint(0, axis, gin.astype(g.dtype)).astype(np.float64)
+        ref = op.DT(gin, axis)
+        assert np.abs(out - ref).max() <= tol * np.abs(ref).max(), (axis, np.abs(out - ref).max())
+        if prec == "fp64":
+            lhs = float(np.sum(g.derivative(0, axis, f) * gin))
+            rhs = float(np.sum(f * out))
+            assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
+    g.close()
+
+
+def _case(kind, prec):
+    if kind == "acoustic":
+        w, model = acoustic2d_gradient_case(precision=prec)
+    else:
+        w, model = elastic3d_gradient_case(precision=prec)
+    _, _, d_obs = oadj.misfit_gradient(w, {f: np.zeros((w.steps, len(i))) for f, i in w.receivers.items()},
+                                       w.steps, model=mean_model(model))
+    return w, model, d_obs
+
+
+def _obs_array(w, d_obs):
+    """The oracle's per-field traces as one [steps, n_receivers] array in the library's receiver order."""
+    from paper_2301_05127_gb300 import FIELDS
+
+    order = sorted(w.receivers, key=lambda f: FIELDS[f])
+    return np.concatenate([np.asarray(d_obs[f]) for f in order], axis=1)
+
+
+def _gpu_gradient(pkg, w, d_obs, checkpoint_every=0):
+    g = pkg.Grid.from_workloads([w])
+    J, grads = g.gradient(0, _obs_array(w, d_obs), w.steps, checkpoint_every)
+    g.close()
+    return J, grads
+
+
+@pytest.mark.parametrize("kind", ["acoustic", "elastic"])
+def test_gradient_matches_oracle_fp64(pkg, kind):
+    w, model, d_obs = _case(kind, "fp64")
+    J0, g0, _ = oadj.misfit_gradient(w, d_obs, w.steps, model=model)
+    J, g = _gpu_gradient(pkg, w, d_obs)
+    assert abs(J - J0) <= 1e-10 * J0, (J, J0)
+    for k in ("vp", "vs", "rho"):
+        if g0[k] is None:
+            continue
+        err = np.abs(g[k] - g0[k]).max() / np.abs(g0[k]).max()
+        assert err < 1e-9, (k, err)
+
+
+@pytest.mark.parametrize("kind", ["acoustic", "elastic"])
+def test_gradient_matches_oracle_fp32(pkg, kind):
+    w, model, d_obs = _case(kind, "fp64")
+    J0, g0, _ = oadj.misfit_gradient(w, d_obs, w.steps, model=model)
+    J, g = _gpu_gradient(pkg, dataclasses.replace(w, precision="fp32_kahan"), d_obs)
+    assert abs(J - J0) <= 1e-4 * J0, (J, J0)
+    for k in ("vp", "vs", "rho"):
+        if g0[k] is None:
+            continue
+        err = np.abs(g[k] - g0[k]).max() / np.abs(g0[k]).max()
+        assert err < 1e-3, (k, err)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(pkg):
+    """Recomputation from checkpoints reproduces the forward run exactly, so every interval gives the same bits."""
+    w, model, d_obs = _case("elastic", "fp32")
+    ref = _gpu_gradient(pkg, w, d_obs, checkpoint_every=w.steps)
+    for c in (1, 5, 0):
+        J, g = _gpu_gradient(pkg, w, d_obs, checkpoint_every=c)
+        assert J == ref[0]
+        for k in ("vp", "vs", "rho"):
+            assert np.array_equal(g[k], ref[1][k]), (c, k)
+
+
+def test_autograd_and_finite_differences(pkg):
+    import torch
+
+    w, model, d_obs = _case("elastic", "fp64")
+    dev = torch.device("cuda")
+    vp, vs, rho = (torch.tensor(a, device=dev, requires_grad=True) for a in model)
+    obs = torch.tensor(_obs_array(w, d_obs), device=dev)
+    from paper_2301_05127_gb300.autograd import seismogram_misfit
+
+    grid = pkg.Grid.from_workloads([w])
+    J = seismogram_misfit(vp, vs, rho, grid, 0, obs, w.steps)
+    J.backward()
+    J0, g0 = _gpu_gradient(pkg, w, d_obs)
+    assert float(J.detach()) == J0
+    np.testing.assert_array_equal(vp.grad.cpu().numpy(), g0["vp"])
+    np.testing.assert_array_equal(rho.grad.cpu().numpy(), g0["rho"])
+    # central differences of the GPU misfit along a smooth direction (zero where vp is largest, so the
+    # absorbing profile stays fixed)
+    d = random_field(w.shape, 77, 2.0)
+    d.reshape(-1)[np.argmax(model[0])] = 0.0
+    for name, ref in (("vp", model[0]), ("vs", model[1]), ("rho", model[2])):
+        eps = 1e-4
+        Js = []
+        for sgn in (1.0, -1.0):
+            m = dict(vp=model[0], vs=model[1], rho=model[2])
+            m[name] = ref + sgn * eps * d * ref
+            grid.set_model(0, m["vp"], m["vs"], m["rho"])
+            Js.append(grid.gradient(0, _obs_array(w, d_obs), w.steps)[0])
+        fd = (Js[0] - Js[1]) / (2 * eps)
+        an = float(np.sum(g0[name] * d * ref))
+        assert abs(fd - an) <= 1e-5 * abs(an), (name, fd, an)
+    grid.close()
+
+
+def test_heterogeneous_elastic_full_geometry(pkg):
+    """193^3 points in 4 x 4 x 4 patches (n_nb 20, 20-point layers): data from the heterogeneous model, gradient
+    at the homogeneous start model after 420 steps (the direct wave has reached the receiver plane), FP32 with
+    compensated updates against the FP64 GPU form."""
+    true = elastic3d_heterogeneous(steps=420)
+    start = elastic3d_heterogeneous(steps=420, true_model=False)
+    g = pkg.Grid.from_workloads([true])
+    g.step(420)
+    obs = g.record(0)["_all"].astype(np.float64)
+    g.close()
+    res = {}
+    for prec in ("fp32_kahan", "fp64"):
+        g = pkg.Grid.from_workloads([dataclasses.replace(start, precision=prec)])
+        res[prec] = g.gradient(0, obs, 420)
+        g.close()
+    J32, g32 = res["fp32_kahan"]
+    J64, g64 = res["fp64"]
+    assert J64 > 0 and abs(J32 - J64) <= 1e-3 * J64, (J32, J64)
+    for k in ("vp", "vs", "rho"):
+        assert np.isfinite(g32[k]).all()
+        err = np.abs(g32[k] - g64[k]).max() / np.abs(g64[k]).max()
+        assert err < 1e-2, (k, err)

@@ -1,14 +1,13 @@
 """Pins of the oracle's discrete adjoint (CPU): the PML sub-flow coefficients against the forward sub-flow,
 dot-product tests of every transposed sub-step (<lam, L u> = <L^T lam, u> for random u, lam), and the misfit
 gradient against central finite differences of the forward oracle for vp, vs and rho."""
-import dataclasses
 
 import numpy as np
 import pytest
 
 from oracle import adjoint as adj
 from oracle.wave import ELASTIC_FIELDS, PML, Operator
-from synth import acoustic2d_small, elastic3d_homogeneous, random_field
+from synth import acoustic2d_gradient_case, elastic3d_gradient_case, mean_model, random_field
 
 
 def _pml(n, h, width, c_max=3000.0, f0=30.0):
@@ -115,33 +114,12 @@ def test_elastic_substeps_dot_product(with_pml):
 
 
 def _acoustic_case():
-    """25^2 points in 2 x 2 patches, 5-point layer, smooth random vp and rho, a 60 Hz source and pressure and
-    velocity receivers on the row z = 2 (inside the layer) and z = 20."""
-    w = acoustic2d_small(n=24, p=2, n_nb=6, steps=40, pml_width=5)
-    shape = w.shape
-    g1, g2 = random_field(shape, 11, 2.0), random_field(shape, 12, 2.0)
-    vp = 2000.0 * (1 + 0.05 * g1)
-    rho = 1000.0 * (1 + 0.05 * g2)
-    rows = np.concatenate([2 * 25 + np.arange(25), 20 * 25 + np.arange(25)]).astype(np.int64)
-    w = dataclasses.replace(w, f0=60.0, t0=1.2 / 60.0, dt=0.4 * 10.0 / vp.max(),
-                            receivers={"sigma": rows, "v1": rows, "v3": rows},
-                            model_fn=lambda: (vp, None, rho))
-    return w, (vp, None, rho)
+    return acoustic2d_gradient_case()
 
 
 def _elastic_case():
-    """13^3 points in 2 x 2 x 2 patches, 3-point layer, smooth random vp, vs, rho, explosive + body-force source,
-    v1..v3 and s33 receivers on the plane z = 1."""
-    w = elastic3d_homogeneous(n=12, p=2, n_nb=4, steps=24, pml_width=3)
-    shape = w.shape
-    vp = 3000.0 * (1 + 0.05 * random_field(shape, 21, 2.0))
-    vs = 1730.0 * (1 + 0.05 * random_field(shape, 22, 2.0))
-    rho = 2000.0 * (1 + 0.05 * random_field(shape, 23, 2.0))
-    plane = (13 * 13 + np.arange(13 * 13)).astype(np.int64)
-    w = dataclasses.replace(w, f0=80.0, t0=1.2 / 80.0, dt=0.4 * 10.0 / vp.max(), src_kinds=("explosive", "force_z"),
-                            receivers={"v1": plane, "v2": plane, "v3": plane, "s33": plane},
-                            model_fn=lambda: (vp, vs, rho))
-    return w, (vp, vs, rho)
+    """Explosive source plus a body force, so that the force term of the b gradient is checked too."""
+    return elastic3d_gradient_case(src_kinds=("explosive", "force_z"))
 
 
 def _direction(shape, seed, ref):
@@ -157,8 +135,7 @@ def test_gradient_matches_finite_differences(case):
     w, (vp, vs, rho) = _acoustic_case() if case == "acoustic" else _elastic_case()
     steps = w.steps
     # observed data: the traces of a homogeneous model
-    base = (np.full(w.shape, float(vp.mean())), None if vs is None else np.full(w.shape, float(vs.mean())),
-            np.full(w.shape, float(rho.mean())))
+    base = mean_model((vp, vs, rho))
     _, _, d_obs = adj.misfit_gradient(w, {f: np.zeros((steps, len(i))) for f, i in w.receivers.items()}, steps,
                                       model=base)
     J, grads, _ = adj.misfit_gradient(w, d_obs, steps, model=(vp, vs, rho))
