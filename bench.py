@@ -175,6 +175,55 @@ def _batched_leg(torch, pkg, units, warmup_units, k):
             "autotune": tune, "launches": launches, "l2": "working set 4.5 GB, no flush"}
 
 
+def _elastic_leg(torch, pkg, steps, warmup, flush):
+    """The homogeneous 3-D elastic workload (257^3 points, 4 x 4 x 4 patches, n_nb = 20, 20-point layers,
+    explosive + shear source, v1..v3 receivers on z = 0), FP32 with compensated updates, per-step events with an
+    L2 flush in between; per-kernel times from the library's events."""
+    from synth import elastic3d_homogeneous
+
+    w = elastic3d_homogeneous(precision="fp32_kahan")
+    g = pkg.Grid.from_workloads([w])
+    g.step(warmup)
+    g.sync()
+    g.profile(True)
+    ms = _timed_steps(torch, g, steps, flush)
+    kern = {k: g.profile_read(k) for k in ("elastic_x", "elastic_y", "elastic_z")}
+    g.close()
+    ms_step = sum(ms) / len(ms)
+    peak, kind = _peaks()
+    # B per point-step of the five passes with a constant model (FP32, compensated stress and velocity
+    # updates): BX 24, BY 28, BZ 140, AX 36, AY 72 (every array a pass must touch, once)
+    alg = 300
+    value = w.points / (ms_step * 1e-3)
+    return {"workload": "elastic3d_homogeneous 257^3 pts, 4x4x4 patches (M=64), n_nb=20, PML 20, FP32 + Kahan",
+            "value": value, "unit": UNIT, "ms_per_step": ms_step,
+            "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items()},
+            "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9),
+            "peak_kind": peak_kind_note(kind), "l2": "flushed between timed steps"}
+
+
+def _adjoint_leg(steps):
+    """Misfit gradient on the heterogeneous 3-D elastic geometry (193^3 points, 4 x 4 x 4 patches, n_nb = 20,
+    FP32 + Kahan) at the homogeneous start model: forward with checkpoints, segment recomputation and the adjoint,
+    timed around the library call (includes its host work: residual, chain rule)."""
+    import paper_2301_05127_gb300 as pkg
+    from synth import elastic3d_heterogeneous
+
+    w = elastic3d_heterogeneous(steps=steps, true_model=False)
+    g = pkg.Grid.from_workloads([w])
+    obs = np.zeros((steps, len(w.receivers["v3"])))
+    g.gradient(0, obs, 4)  # warm-up (allocations)
+    g.sync()
+    t0 = time.perf_counter()
+    J, _ = g.gradient(0, obs, steps)
+    wall = time.perf_counter() - t0
+    g.close()
+    return {"workload": f"elastic3d_heterogeneous start model 193^3 pts, 4x4x4 patches, {steps} steps, FP32 + Kahan, "
+                        f"checkpoints every {int(math.ceil(math.sqrt(steps)))} steps",
+            "ms_per_step": 1e3 * wall / steps, "value": w.points * steps / wall, "unit": UNIT + " (forward+adjoint)",
+            "misfit": J}
+
+
 def peak_kind_note(kind):
     return "of measured" if kind == "measured" else "of fallback"
 
@@ -265,8 +314,10 @@ def run_ours(args):
     g64.close()
     g.close()
 
-    # --- batched multi-shot survey ----------------------------------------------------------------------------
+    # --- batched multi-shot survey, 3-D elastic step, misfit gradient ---------------------------------------
     batched = _batched_leg(torch, pkg, units=3, warmup_units=1, k=10) if not args.no_batched else None
+    elastic = _elastic_leg(torch, pkg, steps=5, warmup=3, flush=flush) if not args.no_batched else None
+    adjoint = _adjoint_leg(steps=60) if not args.no_batched else None
 
     # --- end to end through the public API with host buffers ---------------------------------------------
     ge = pkg.Grid.from_workloads([w])
@@ -309,6 +360,8 @@ def run_ours(args):
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms},
             "batched": batched,
+            "elastic": elastic,
+            "adjoint": adjoint,
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s_timed_region": t_wall,
@@ -362,7 +415,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-shot batched leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched, elastic and gradient legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
