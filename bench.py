@@ -126,15 +126,22 @@ def _timed_steps(torch, g, steps, flush):
     return [a.elapsed_time(b) for a, b in times]
 
 
+KERNELS = ("acoustic_x", "acoustic_z", "acoustic_z2")
+
+
 def _alg_bytes_per_point(kernel, esize, kahan, b_array):
-    """Algorithmic DRAM bytes per grid point of one launch: every array the kernel must touch, once (the density
-    of the benchmark model is constant, so the buoyancy is a scalar and no b array is read)."""
+    """Algorithmic DRAM bytes per grid point of one launch of the FP32 step's kernels: every array the kernel must
+    touch, once (the density of the benchmark model is constant, so the buoyancy is a scalar and no b array is
+    read)."""
     if kernel == "acoustic_x":
         # read v1, sigma, kappa, d_z v3; write sigma, v1 (+ compensation of sigma and v1, read and written)
         n = 4 + 2 + (4 if kahan else 0) + (1 if b_array else 0)
+    elif kernel == "acoustic_z":
+        # read sigma, v3; write v3 (+ compensation of v3, read and written)
+        n = 2 + 1 + (2 if kahan else 0) + (1 if b_array else 0)
     else:
-        # read sigma, v3; write v3, d_z v3 (+ compensation of v3, read and written)
-        n = 2 + 2 + (2 if kahan else 0) + (1 if b_array else 0)
+        # read v3; write d_z v3
+        n = 2
     return n * esize
 
 
@@ -275,14 +282,14 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall
     clocks = clk.stop()
     launches = g.profile_read(-1)[1]
-    kern = {k: g.profile_read(k) for k in ("acoustic_x", "acoustic_z", "gather")}
+    kern = {k: g.profile_read(k) for k in KERNELS + ("gather",)}
     g.profile(False)
     sum_ms = max_over_ranks(sum(step_ms))
     ms_per_step = sum_ms / args.steps
     value = ws * pts / (ms_per_step * 1e-3)
 
     # dominant kernel roofline
-    dom = max(("acoustic_x", "acoustic_z"), key=lambda k: kern[k][0])
+    dom = max(KERNELS, key=lambda k: kern[k][0])
     dom_ms = kern[dom][0] / max(kern[dom][1], 1)
     alg = _alg_bytes_per_point(dom, 4, True, False) * pts
     peak, peak_kind = _peaks()
@@ -355,6 +362,8 @@ def run_ours(args):
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "alg_bytes_per_launch": alg, "avg_launch_ms": dom_ms},
             "kernels_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in kern.items()},
+            "kernels_frac_of_peak": {k: _alg_bytes_per_point(k, 4, True, False) * pts / (kern[k][0] / kern[k][1] * 1e-3)
+                                     / (peak * 1e9) for k in KERNELS if kern[k][1]},
             "fp64": {"value": ws * pts / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "unit": UNIT},
             "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + args.steps},
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,

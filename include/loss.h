@@ -212,6 +212,10 @@ enum {
   LOSS_KERNEL_ELASTIC_Z = 6,  /* 3-D elastic passes on z lines */
   LOSS_KERNEL_CLOCK = 7,      /* batched schedule: end-of-step advance of the device step counters */
   LOSS_KERNEL_ADJOINT = 8,    /* adjoint terms and the transposed derivative (loss_gradient, loss_derivative_adjoint) */
+  LOSS_KERNEL_ACOUSTIC_X2 = 9,  /* 2-D acoustic FP32 tiles: x part of the velocity sub-step (the stress sub-step is
+                                   LOSS_KERNEL_ACOUSTIC_X) */
+  LOSS_KERNEL_ACOUSTIC_Z2 = 10, /* 2-D acoustic FP32 tiles: d_z v3 for the next step (the z velocity part is
+                                   LOSS_KERNEL_ACOUSTIC_Z) */
   LOSS_NUM_KERNELS = 16
 };
 
@@ -239,6 +243,16 @@ loss_status_t loss_set_tile(loss_handle_t handle, int32_t kernel, int32_t thread
  * Other handles (3-D elastic) always use per-shot launches.  Per-kernel timing (loss_profile) is not available
  * for steps replayed from a graph; launches are counted.  LOSS_E_ARG if graph_steps < 0. */
 loss_status_t loss_set_schedule(loss_handle_t handle, int32_t batched, int32_t graph_steps);
+
+/* Kernel family of the per-shot FP32 2-D acoustic step: LOSS_KERNELS_LINE = whole grid lines on chip with the
+ * chunked Thomas solve of the patch systems (the form every other grid and the batched schedule use);
+ * LOSS_KERNELS_CONVOLUTION (the default) = the truncated-convolution form: the same patch systems solved through
+ * the closed-form inverse of the (1, 4, 1) operator, truncated where |sqrt(3) - 2|^k < 1e-9, with exact patch-end
+ * corrections from the PMBC junction values (x rows pipelined through TMA bulk copies, z lines on independent
+ * 32-column x one-patch tiles).  Both agree with the FP64 oracle at the FP32 tolerance; they differ in rounding.
+ * LOSS_E_ARG for another value. */
+enum { LOSS_KERNELS_LINE = 0, LOSS_KERNELS_CONVOLUTION = 1 };
+loss_status_t loss_set_kernels(loss_handle_t handle, int32_t family);
 
 /* One autotuner result: the tile shape chosen for a kernel family and its measured mean launch time. */
 typedef struct {

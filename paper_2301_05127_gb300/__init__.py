@@ -80,12 +80,13 @@ _PROTOS = {
     "loss_set_launch": (_I32, [_H, _I32, _I32, _I32]),
     "loss_set_tile": (_I32, [_H, _I32, _I32, _I32]),
     "loss_set_schedule": (_I32, [_H, _I32, _I32]),
+    "loss_set_kernels": (_I32, [_H, _I32]),
     "loss_autotune": (_I32, [_H, _I32, ctypes.POINTER(TuneEntry), _I32, ctypes.POINTER(_I32)]),
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
 KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
-           "elastic_z": 6, "clock": 7, "adjoint": 8}
+           "elastic_z": 6, "clock": 7, "adjoint": 8, "acoustic_x2": 9, "acoustic_z2": 10}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -368,6 +369,10 @@ class Grid:
     def set_tile(self, kernel, threads_per_block=0, chunk_log2=0):
         kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         _check(lib().loss_set_tile(self.h, kid, int(threads_per_block), int(chunk_log2)), self.h)
+
+    def set_kernels(self, family: str = "convolution"):
+        """Kernel family of the per-shot FP32 2-D acoustic step: "line" or "convolution" (loss_set_kernels)."""
+        _check(lib().loss_set_kernels(self.h, {"line": 0, "convolution": 1}[family]), self.h)
 
     def set_schedule(self, batched: bool = True, graph_steps: int = 0):
         _check(lib().loss_set_schedule(self.h, 1 if batched else 0, int(graph_steps)), self.h)

@@ -81,6 +81,47 @@ std::vector<double> pmbc_weights_scaled(int n, int p, int n_nb) {
   return W;
 }
 
+// Junction-correction weights of the truncated-convolution form (loss_fir.cuh): D_j = phi_j - eF_j as weights on
+// the field at positions jM + m, |m| <= R = max(n_nb, K): the PMBC weights (scaled by h/3) minus the weights of
+// eF_j = a sum_{k=1..K} r^{k-1} (f_{c+k} - f_{c-k}) with the line continued by odd reflection beyond its ends
+// (f_{-q} = 2 f_0 - f_q, f_{n+q} = 2 f_n - f_{n-q}, q clamped to the line).  Formed in FP64; away from the
+// physical ends the two weight sets agree to O(r^K), so the FP32 sum of D f carries no cancellation.
+std::vector<float> fir_delta_weights(int n, int p, int n_nb, int K) {
+  const std::vector<double> W = pmbc_weights_scaled(n, p, n_nb);
+  const int M = n / p;
+  const int R = std::max(n_nb, K);
+  const int wl = 2 * R + 1;
+  const double r = std::sqrt(3.0) - 2.0;
+  const double a = (1.0 - r * r) / (2.0 * std::sqrt(3.0));
+  std::vector<double> D((size_t)(p + 1) * wl, 0.0);
+  for (int j = 0; j <= p; ++j) {
+    const int c = j * M;
+    double* Dj = D.data() + (size_t)j * wl + R;  // Dj[m], m = -R..R
+    for (int m = -n_nb; m <= n_nb; ++m)
+      if (c + m >= 0 && c + m <= n) Dj[m] += W[(size_t)j * (2 * n_nb + 1) + (m + n_nb)];
+    auto add = [&](int pos, double w) {
+      if (pos >= 0 && pos <= n) {
+        Dj[pos - c] += w;
+      } else if (pos < 0) {
+        const int q = std::min(-pos, n);
+        Dj[0 - c] += 2.0 * w;
+        Dj[q - c] -= w;
+      } else {
+        const int q = std::max(n - (pos - n), 0);
+        Dj[n - c] += 2.0 * w;
+        Dj[q - c] -= w;
+      }
+    };
+    double rk = 1.0;
+    for (int k = 1; k <= K; ++k) {
+      add(c + k, -a * rk);
+      add(c - k, a * rk);
+      rk *= r;
+    }
+  }
+  return std::vector<float>(D.begin(), D.end());
+}
+
 void thomas_tables(std::vector<double>& t64, std::vector<float>& t32) {
   t64.assign(kTableLen, 0.0);
   t32.assign(kTableLen, 0.0f);
@@ -460,6 +501,9 @@ loss_status_t loss_create_grid(const loss_grid_desc_t* descs, int32_t n_shots, c
       cudaMemcpyAsync(h->t32, t32.data(), kTableLen * sizeof(float), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess)
     return bail(LOSS_E_CUDA);
+  if (dev_alloc(h, sizeof(int), (void**)&h->dflag) != LOSS_OK ||
+      cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess)
+    return bail(LOSS_E_NOMEM);
   h->shots.resize(n_shots);
   for (int i = 0; i < n_shots; ++i) {
     h->shots[i].d = descs[i];
@@ -502,6 +546,16 @@ loss_status_t loss_set_tile(loss_handle_t h, int32_t kernel, int32_t threads_per
     return fail(h, LOSS_E_ARG, "threads_per_block must be 0 or in 32..1024");
   h->tile_threads[kernel] = threads_per_block;
   h->chunk_log2[kernel] = chunk_log2;
+  return LOSS_OK;
+}
+
+loss_status_t loss_set_kernels(loss_handle_t h, int32_t family) {
+  LOSS_TRY(guard(h));
+  if (family != LOSS_KERNELS_LINE && family != LOSS_KERNELS_CONVOLUTION)
+    return fail(h, LOSS_E_ARG, "unknown kernel family");
+  for (const Shot& s : h->shots)
+    if (s.staggered) return fail(h, LOSS_E_STATE, "choose the kernel family before the first step");
+  h->tiled = family;
   return LOSS_OK;
 }
 
@@ -646,7 +700,11 @@ loss_status_t loss_profile_read(loss_handle_t h, int32_t kernel, double* total_m
 
 loss_status_t loss_sync(loss_handle_t h) {
   LOSS_TRY(guard(h));
-  return cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize"));
+  int flag = 0;
+  if (h->dflag) LOSS_TRY(cuda_check(h, cudaMemcpy(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost), "read flag"));
+  if (flag) return fail(h, LOSS_E_TIMEOUT, "a kernel gave up waiting for its staged data");
+  return LOSS_OK;
 }
 
 static loss_status_t get_shot(loss_ctx* h, int32_t shot, Shot** s) {

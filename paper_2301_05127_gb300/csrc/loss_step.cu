@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "loss_fir.cuh"
 #include "loss_host.h"
 
 namespace lossk {
@@ -134,6 +135,88 @@ static loss_status_t ac_z(loss_ctx* h, Shot& s, double acoef, int do_tmp) {
   return cuda_check(h, launch_ac_z<T, K>(a, logc, threads, h->stream), "acoustic z kernel");
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// FP32 tiles in the truncated-convolution form (loss_kernels_tiled.cu): four launches per step.
+static bool tiled_ok(const loss_ctx* h, const Shot& s) {
+  if (!h->tiled || s.esize != 4 || s.dim != 2 || s.d.physics != LOSS_ACOUSTIC) return false;
+  const int Mz = (int)(s.n[0] / s.p[0]);
+  return Mz <= 512 && std::max(s.d.n_nb, FirLen<float>::K) <= 64;
+}
+
+// z tiles: 32 columns x one patch, C = 16 positions per thread; x tiles: R rows x one patch, C = 8.
+static TileGeom tile_geom(const Shot& s, int k, int* threads) {
+  TileGeom t{};
+  t.n = (int)s.n[k];
+  t.p = s.p[k];
+  t.M = t.n / t.p;
+  t.n_nb = s.d.n_nb;
+  t.px = s.px;
+  t.W = s.W[k];
+  const FirConst fc = fir_const(t.M);
+  t.s3h = (float)(3.0 / s.h[k]);
+  t.r = (float)fc.r;
+  t.a = (float)fc.a;
+  t.rho = (float)fc.rho;
+  t.inv = (float)fc.inv;
+  t.Wd = s.Wd[k];
+  t.Rd = std::max(s.d.n_nb, FirLen<float>::K);
+  t.H = t.Rd;
+  if (k == 0) {
+    t.ncross = (int)s.len[2];
+    t.ntl = (t.ncross + 31) / 32;
+    t.R = 32;
+    *threads = 32 * ((t.M + 15) / 16);
+  } else {
+    t.ncross = (int)s.len[0];
+    t.ntl = t.ncross;
+    t.R = 1;
+    *threads = (((t.n + 7) / 8 + 31) / 32) * 32;
+  }
+  return t;
+}
+
+// Junction-correction weights of axis slot k in device memory (FP32 truncated-convolution kernels).
+static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
+  if (s.Wd[k]) return LOSS_OK;
+  const std::vector<float> D = fir_delta_weights((int)s.n[k], s.p[k], s.d.n_nb, FirLen<float>::K);
+  void* p = nullptr;
+  LOSS_TRY(dev_alloc(h, D.size() * sizeof(float), &p));
+  LOSS_TRY(cuda_check(h, cudaMemcpyAsync(p, D.data(), D.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+                      "copy junction weights"));
+  LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  s.Wd[k] = (float*)p;
+  return LOSS_OK;
+}
+
+// x part of the FP32 step (sub-step B and the x part of A, or the latter alone): the pipelined row kernel when a
+// row fits one block, else the line kernel.
+template <bool K>
+static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double amp) {
+  const size_t xsm = (size_t)(2 * 6 + 1) * ((s.n[2] + 1 + 3) & ~3) * 4 +
+                     (size_t)(s.p[2] + 1) * (2 * std::max(s.d.n_nb, FirLen<float>::K) + 1) * 4;
+  if (s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 && xsm + 2048 <= (size_t)h->smem_optin) {
+    LOSS_TRY(ensure_delta_weights(h, s, 2));
+    int threads;
+    TileGeom t = tile_geom(s, 2, &threads);
+    t.ncross = (int)s.len[0];
+    const unsigned mm = (unsigned)((((uint64_t)1 << 32) + (uint64_t)t.M - 1) / (uint64_t)t.M);
+    const AcXArgs<float> a = ac_x_args<float>(h, s, LineGeom{}, do_B, acoef, amp);
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
+    return cuda_check(h, launch_xp<K>(a, t, mm, h->dflag, h->num_sms, h->stream), "acoustic x kernel");
+  }
+  return ac_x<float, K>(h, s, do_B, acoef, amp);
+}
+
+template <bool K>
+static loss_status_t tz(loss_ctx* h, Shot& s, int mode, double acoef) {
+  LOSS_TRY(ensure_delta_weights(h, s, 0));
+  int threads;
+  const TileGeom t = tile_geom(s, 0, &threads);
+  const AcZArgs<float> a = ac_z_args<float>(h, s, LineGeom{}, acoef, 0);
+  LaunchScope ls(h, mode == 1 ? LOSS_KERNEL_ACOUSTIC_Z : LOSS_KERNEL_ACOUSTIC_Z2);
+  return cuda_check(h, launch_tz<K>(a, t, mode, threads, h->stream), "acoustic z tile kernel");
+}
+
 template <typename T>
 static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mode) {
   if (s.n_rcv == 0) return LOSS_OK;
@@ -159,18 +242,36 @@ static double pressure_amp(const Shot& s, int64_t n) {
   return dt * s.src_norm * ricker((double)n * dt + 0.5 * dt, s.src_f0, s.src_t0);
 }
 
+// The staggered start: half velocity sub-step, then d_z v3 for the first B.
+template <typename T, bool K>
+static loss_status_t acoustic2d_start(loss_ctx* h, Shot& s) {
+  const double dt = s.d.dt;
+  if (sizeof(T) == 4 && tiled_ok(h, s)) {
+    LOSS_TRY(xpart<K>(h, s, 0, 0.5 * dt, 0.0));
+    LOSS_TRY(tz<K>(h, s, 1, 0.5 * dt));
+    return tz<K>(h, s, 2, 0.0);
+  }
+  LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * dt, 0.0)));
+  return ac_z<T, K>(h, s, 0.5 * dt, 1);
+}
+
 template <typename T, bool K>
 static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
   const double dt = s.d.dt;
   LOSS_TRY(ensure_rdelta(h, s));
   if (!s.staggered) {
-    LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * dt, 0.0)));
-    LOSS_TRY((ac_z<T, K>(h, s, 0.5 * dt, 1)));
+    LOSS_TRY((acoustic2d_start<T, K>(h, s)));
     s.staggered = true;
   }
   LOSS_TRY(gather_fields<T>(h, s, true, 0));  // v at t_{n+1/2}
-  LOSS_TRY((ac_x<T, K>(h, s, 1, dt, pressure_amp(s, s.step))));
-  LOSS_TRY((ac_z<T, K>(h, s, dt, 1)));
+  if (sizeof(T) == 4 && tiled_ok(h, s)) {
+    LOSS_TRY(xpart<K>(h, s, 1, dt, pressure_amp(s, s.step)));
+    LOSS_TRY(tz<K>(h, s, 1, dt));
+    LOSS_TRY(tz<K>(h, s, 2, 0.0));
+  } else {
+    LOSS_TRY((ac_x<T, K>(h, s, 1, dt, pressure_amp(s, s.step))));
+    LOSS_TRY((ac_z<T, K>(h, s, dt, 1)));
+  }
   LOSS_TRY(gather_fields<T>(h, s, true, 1));   // (v_{n+1/2} + v_{n+3/2}) / 2 = v_{n+1}
   LOSS_TRY(gather_fields<T>(h, s, false, 0));  // sigma_{n+1}
   if (s.n_rcv) ++s.rcv_steps;
@@ -181,6 +282,12 @@ static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
 template <typename T, bool K>
 static loss_status_t acoustic2d_unstagger(loss_ctx* h, Shot& s) {
   const double dt = s.d.dt;
+  if (sizeof(T) == 4 && tiled_ok(h, s)) {
+    LOSS_TRY(xpart<K>(h, s, 0, -0.5 * dt, 0.0));
+    LOSS_TRY(tz<K>(h, s, 1, -0.5 * dt));
+    s.staggered = false;
+    return LOSS_OK;
+  }
   LOSS_TRY((ac_x<T, K>(h, s, 0, -0.5 * dt, 0.0)));
   LOSS_TRY((ac_z<T, K>(h, s, -0.5 * dt, 0)));
   s.staggered = false;
@@ -633,16 +740,9 @@ loss_status_t stagger_shot(loss_ctx* h, Shot& s) {
   LOSS_TRY(ensure_rdelta(h, s));
   const double dt = s.d.dt;
   if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {
-    if (s.esize == 8) {
-      LOSS_TRY((ac_x<double, false>(h, s, 0, 0.5 * dt, 0.0)));
-      LOSS_TRY((ac_z<double, false>(h, s, 0.5 * dt, 1)));
-    } else if (s.kahan) {
-      LOSS_TRY((ac_x<float, true>(h, s, 0, 0.5 * dt, 0.0)));
-      LOSS_TRY((ac_z<float, true>(h, s, 0.5 * dt, 1)));
-    } else {
-      LOSS_TRY((ac_x<float, false>(h, s, 0, 0.5 * dt, 0.0)));
-      LOSS_TRY((ac_z<float, false>(h, s, 0.5 * dt, 1)));
-    }
+    if (s.esize == 8) LOSS_TRY((acoustic2d_start<double, false>(h, s)));
+    else if (s.kahan) LOSS_TRY((acoustic2d_start<float, true>(h, s)));
+    else LOSS_TRY((acoustic2d_start<float, false>(h, s)));
   } else if (s.d.physics == LOSS_ELASTIC) {
     const double tn = (double)s.step * dt;
     if (s.esize == 8) LOSS_TRY((elastic_A<double, false>(h, s, 0.5 * dt, tn)));

@@ -56,6 +56,19 @@ struct DerivArgs {
 // Largest block of the persistent batched kernels.
 constexpr int kBatchThreads = 512;
 
+// Tile geometry of the FP32 truncated-convolution kernels (loss_kernels_tiled.cu): derivative axis of n intervals
+// in p patches of M, halo H positions per side, ntl tiles across the other axis (z tiles: groups of 32 columns,
+// x tiles: groups of R rows), ncross points along the other axis, row pitch px; W = PMBC weights of the axis
+// (scaled by h/3); r, a, rho = r^M and inv = 1 / (1 - rho^2) of loss_fir.cuh.
+struct TileGeom {
+  int n, p, M, n_nb, H, ntl, R, ncross;
+  int64_t px;
+  const double* W;
+  const float* Wd;   // junction-correction weights [(p + 1)][2 Rd + 1] (PMBC weights minus convolution weights)
+  int Rd;            // their half width, max(n_nb, K)
+  float s3h, r, a, rho, inv;
+};
+
 // Device-side step counters of one shot, used by launches whose arguments do not change from step to step
 // (persistent batched launches and captured CUDA graphs): step = index n of the step being taken, row = trace row
 // the step's receiver values go to; both advance once per step (row by row_inc, 1 when the shot records).

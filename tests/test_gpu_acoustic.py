@@ -32,8 +32,10 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def _compare(pkg, w, prec, steps, every=50):
+def _compare(pkg, w, prec, steps, every=50, family=None):
     g = pkg.Grid.from_workloads([w], precision=prec)
+    if family:
+        g.set_kernels(family)
     sim = Simulation(w)
     fields = ("sigma", "v1", "v3")
     peak = {f: 0.0 for f in fields}
@@ -158,3 +160,33 @@ def test_velocity_receivers_inside_the_layer(pkg):
         ref = sim.trace_array(f)
         assert np.abs(rec[f] - ref).max() <= 1e-11 * np.abs(ref).max(), f
     g.close()
+
+
+@pytest.mark.parametrize("family", ["line", "convolution"])
+@pytest.mark.parametrize("geom", [
+    # (n_z, n_x, p_z, p_x, n_nb, layer): patch lengths shorter than the convolution's truncation length (16),
+    # not multiples of 8 (x falls back to the line kernel), a single-warp z tile, x extents that are not multiples
+    # of 32, halo widths above 16, one patch per axis
+    (24, 24, 2, 2, 6, 5),
+    (36, 40, 3, 5, 8, 6),
+    (48, 70, 4, 5, 10, 8),
+    (64, 96, 2, 3, 20, 10),
+    (80, 48, 1, 1, 24, 8),
+])
+def test_fp32_kernel_families_on_uneven_geometries(pkg, family, geom):
+    """Both kernel families of the FP32 step against the oracle on geometries chosen to reach the edge cases of
+    the convolution kernels (tiles of one warp, ragged column groups, patch ends within the truncation length,
+    line ends reached by the recursions' warm-up from both sides)."""
+    nz, nx, pz, px, n_nb, layer = geom
+    w = acoustic2d_small(n=max(nz, nx), p=2, n_nb=n_nb, steps=60, pml_width=layer)
+    shape = (nz + 1, nx + 1)
+
+    def model():
+        z = np.arange(nz + 1)[:, None] * np.ones((1, nx + 1))
+        return np.where(z < nz / 2, 2000.0, 2600.0), None, np.full(shape, 1000.0)
+
+    top = np.arange(nx + 1, dtype=np.int64)
+    w = dataclasses.replace(w, n=(nz, nx), p=(pz, px), model_fn=model, src_index=(nz // 2, nx // 3),
+                            receivers={"sigma": top}, f0=60.0, t0=1.2 / 60.0, dt=0.4 * 10.0 / 2600.0)
+    errs = _compare(pkg, w, "fp32_kahan", 60, every=20, family=family)
+    assert max(errs.values()) < TOL["fp32_kahan"], errs

@@ -40,6 +40,7 @@ def _shots(prec="fp64"):
 
 def _run(pkg, ws, batched, graph_steps, chunks):
     g = pkg.Grid.from_workloads(ws)
+    g.set_kernels("line")  # the batched schedule runs the line kernels
     g.set_schedule(batched, graph_steps)
     for c in chunks:
         g.step(c)
@@ -108,6 +109,7 @@ def test_interleaved_reads_and_records(pkg):
 
     def seq(batched, graph_steps):
         g = pkg.Grid.from_workloads(ws)
+        g.set_kernels("line")
         g.set_schedule(batched, graph_steps)
         g.step(10)
         v = g.get_field(1, "v1")
@@ -156,6 +158,7 @@ def test_full_survey_batched(pkg):
     g.set_schedule(True, 3)
     g.step(3)
     r = pkg.Grid.from_workloads(ws)
+    r.set_kernels("line")
     r.set_schedule(False, 0)
     r.step(3)
     for s in range(len(ws)):
