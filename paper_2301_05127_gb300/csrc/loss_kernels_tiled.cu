@@ -196,22 +196,46 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
 struct PlainBun {
   __device__ __forceinline__ int at(int, int pos) const { return pos; }
 };
+// Eight values of chunk s.  Lanes of chunks with (s >> 2) odd read the two 16-byte halves in the other order, so the
+// eight lanes of a quarter warp (chunks 32 bytes apart) hit disjoint banks.
 __device__ __forceinline__ void plain8(const float* __restrict__ row, int s, float (&v)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(row + s * 8);
-  const float4 b = *reinterpret_cast<const float4*>(row + s * 8 + 4);
-  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  const int h = (s >> 2) & 1;
+  const float4 a = *reinterpret_cast<const float4*>(row + s * 8 + 4 * h);
+  const float4 b = *reinterpret_cast<const float4*>(row + s * 8 + 4 - 4 * h);
+  const float4 lo = h ? b : a, hi = h ? a : b;
+  v[0] = lo.x, v[1] = lo.y, v[2] = lo.z, v[3] = lo.w, v[4] = hi.x, v[5] = hi.y, v[6] = hi.z, v[7] = hi.w;
+}
+__device__ __forceinline__ void plain8_store(float* row, int s, const float (&v)[9]) {
+  const int h = (s >> 2) & 1;
+  const float4 lo = make_float4(v[0], v[1], v[2], v[3]), hi = make_float4(v[4], v[5], v[6], v[7]);
+  *reinterpret_cast<float4*>(row + s * 8 + 4 * h) = h ? hi : lo;
+  *reinterpret_cast<float4*>(row + s * 8 + 4 - 4 * h) = h ? lo : hi;
 }
 struct PlainLayout {
   PlainBun bun;
   __device__ __forceinline__ void eight(const float* row, int s, float (&v)[8]) const { plain8(row, s, v); }
+  __device__ __forceinline__ void store8(float* row, int s, const float (&v)[9]) const { plain8_store(row, s, v); }
   __device__ __forceinline__ int chunk(int s) const { return s * 8; }
 };
+
+// Warm-up partial sums of chunk c (first eight values): PA = sum_j r^{7-j} f_{8c+j} (its part of the left sum of
+// chunks c + 1 and c + 2) and PB = sum_j r^j f_{8c+j} (its part of the right sum of chunks c - 1 and c - 2), in
+// the Horner order the consumers would use.
+__device__ __forceinline__ void xf_partials(const float (&f)[8], float r, float& pa, float& pb) {
+  pa = 0.0f;
+  pb = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) pa = f[j] + r * pa;
+#pragma unroll
+  for (int j = 7; j >= 0; --j) pb = f[j] + r * pb;
+}
 
 // e on chunk c of the row (positions 8c .. 8c + len - 1, len = 8, or 9 for the chunk ending at n).
 template <class LAY>
 __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LAY& lay, int c, int len,
                                          const TileGeom& t, int M, unsigned mmagic, const float* __restrict__ dlf,
-                                         const float* __restrict__ rpow, float (&e)[9]) {
+                                         const float* __restrict__ rpow, const float* __restrict__ PA,
+                                         const float* __restrict__ PB, float (&e)[9]) {
   constexpr int K = FirLen<float>::K;  // 16 = two slots
   const int p0 = c << 3;
   const float r = t.r;
@@ -225,18 +249,8 @@ __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LA
   }
   float s = 0.0f;
   if (p0 >= K) {
-    // L = sum_{k=1..16} r^{k-1} f_{p0-k}: the terms of slot c-1 (k = 1..8) and of slot c-2 (k = 9..16) as two
-    // independent Horner chains
-    float a8[8], b8[8];
-    lay.eight(row, c - 2, a8);
-    lay.eight(row, c - 1, b8);
-    float sa = 0.0f, sb = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      sa = a8[j] + r * sa;
-      sb = b8[j] + r * sb;
-    }
-    s = sb + rpow[8] * sa;
+    // L = sum_{k=1..16} r^{k-1} f_{p0-k}: chunk c-1 gives the terms k = 1..8, chunk c-2 those of k = 9..16
+    s = PA[c - 1] + rpow[8] * PA[c - 2];
   } else {
     s = fir_left<float, K>(row, lay.bun, 0, p0, t.n, r);
   }
@@ -249,16 +263,7 @@ __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LA
   float q = 0.0f;
   const int pe = p0 + len - 1;
   if (len == 8 && pe + K <= t.n) {
-    float a8[8], b8[8];
-    lay.eight(row, c + 1, a8);
-    lay.eight(row, c + 2, b8);
-    float qa = 0.0f, qb = 0.0f;
-#pragma unroll
-    for (int j = 7; j >= 0; --j) {
-      qa = a8[j] + r * qa;
-      qb = b8[j] + r * qb;
-    }
-    q = qa + rpow[8] * qb;
+    q = PB[c + 1] + rpow[8] * PB[c + 2];
   } else {
     q = fir_right<float, K>(row, lay.bun, 0, pe, t.n, r);
   }
@@ -301,13 +306,43 @@ __device__ void xf_junctions(const float* __restrict__ row, const BUN& bun, cons
   }
 }
 
+// Layer segments of an x-axis memory variable staged with a row: positions [0, W) and [R0, R0 + SR) (R0 = the
+// layer start n + 1 - W rounded down to 16 bytes).
+struct MemSeg {
+  int W, SL, R0, SR;
+  __device__ __forceinline__ int at(int pos) const { return pos < W ? pos : SL + (pos - R0); }
+  __device__ __forceinline__ int floats() const { return SL + SR; }
+};
+__device__ __forceinline__ MemSeg mem_seg(int n, int W) {
+  MemSeg m;
+  m.W = W;
+  m.SL = (W + 3) & ~3;
+  m.R0 = (n + 1 - W) & ~3;
+  m.SR = (n + 1 - m.R0 + 3) & ~3;
+  return m;
+}
+// PmlAxis::step / ::half with the memory value before the sub-step given (same arithmetic).
+__device__ __forceinline__ float pml_step_m0(const PmlAxis<float>& pa, float m0, float* mem, int64_t gi, int i,
+                                             float g) {
+  const int n1 = pa.n + 1;
+  const float m1 = pa.tab[i] * m0 - pa.tab[n1 + i] * g;
+  mem[gi] = m1;
+  return pa.tab[2 * n1 + i] * (m1 - m0) - pa.tab[3 * n1 + i] * g;
+}
+__device__ __forceinline__ float pml_half_m0(const PmlAxis<float>& pa, float m0, int i, float g) {
+  const int n1 = pa.n + 1;
+  const float m1 = pa.tabh[i] * m0 - pa.tabh[n1 + i] * g;
+  return pa.tabh[2 * n1 + i] * (m1 - m0) - pa.tabh[3 * n1 + i] * g;
+}
+
 // One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY).
 // Contains barriers: every thread of the block must call it.
 template <bool KAHAN, class LAY>
 __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int row,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
-                                     const float* wd, float* dlf) {
+                                     const float* wd, float* dlf, const MemSeg& ms, const float* segB,
+                                     const float* segA, float* PA, float* PB) {
   const int n = t.n, np = n + 1;
   const int M = t.M;
   const int64_t rb = (int64_t)row * t.px;
@@ -328,11 +363,16 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       const int q0 = cc << 3, q1 = q0 + chunk_len(cc) - 1;
       return zlay || (a.pml && (a.xB.in(q0) || a.xB.in(q1))) || (srow && q1 >= a.src.xs - 12 && q0 <= a.src.xs + 12);
     };
+    if (act) {
+      float f8[8];
+      lay.eight(V, c, f8);
+      xf_partials(f8, t.r, PA[c], PB[c]);
+    }
     xf_junctions<16>(V, lay.bun, t, wd, dlf);
     __syncthreads();
     if (act) {
       float e[9];
-      xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, e);
+      xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
       if (slowB(c)) {
 #pragma unroll
         for (int j = 0; j < 9; ++j)
@@ -375,8 +415,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
           }
           sg[j] = v;
         }
-        *reinterpret_cast<float4*>(D + lay.chunk(c)) = make_float4(sg[0], sg[1], sg[2], sg[3]);
-        *reinterpret_cast<float4*>(D + lay.chunk(c) + 4) = make_float4(sg[4], sg[5], sg[6], sg[7]);
+        lay.store8(D, c, sg);
         if (len > 8) D[lay.chunk(c + 1)] = sg[8];
         store_run<8>(a.sigma + rb + p0, len, sg);
         if (KAHAN) store_run<8>(a.csig + rb + p0, len, cs);
@@ -389,7 +428,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       const int k = lay.bun.at(0, pos);
       const float gx = O[pos];
       const float gzv = ST[k];
-      const float inc = (a.pml && a.xB.in(pos)) ? a.xB.step(a.phix, gi, pos, gx) : -a.dt * gx;
+      const float inc = (a.pml && a.xB.in(pos)) ? pml_step_m0(a.xB, segB[ms.at(pos)], a.phix, gi, pos, gx) : -a.dt * gx;
       const float incz = zlay ? a.zB.step(a.phiz, gi, row, gzv) : -a.dt * gzv;
       float delta = SK[k] * (inc + incz);
       if (srow) {
@@ -413,11 +452,16 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     const int q0 = cc << 3, q1 = q0 + chunk_len(cc) - 1;
     return a.pml && (a.xA.in(q0) || a.xA.in(q1));
   };
+  if (act) {
+    float f8[8];
+    lay.eight(D, c, f8);
+    xf_partials(f8, t.r, PA[c], PB[c]);
+  }
   xf_junctions<16>(D, lay.bun, t, wd, dlf);
   __syncthreads();
   if (act) {
     float e[9];
-    xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, e);
+    xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
     if (slowA(c)) {
 #pragma unroll
       for (int j = 0; j < 9; ++j)
@@ -468,8 +512,9 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     const float bb = a.b ? a.b[gi] : a.b0;
     float inc;
     if (a.xA.in(pos)) {
-      const float ih = a.dlt ? a.xA.half(a.psix, gi, pos, gx) : 0.0f;
-      inc = a.xA.step(a.psix, gi, pos, gx);
+      const float m0 = segA[ms.at(pos)];
+      const float ih = a.dlt ? pml_half_m0(a.xA, m0, pos, gx) : 0.0f;
+      inc = pml_step_m0(a.xA, m0, a.psix, gi, pos, gx);
       if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
     } else {
       inc = -a.acoef * gx;
@@ -515,11 +560,18 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
   float* WS = base + 13 * RW;  // junction-correction weights, loaded once
   const int nw = (t.p + 1) * (2 * t.Rd + 1);
   for (int i = threadIdx.x; i < nw; i += blockDim.x) WS[i] = t.Wd[i];
+  // layer segments of the x memory variables (phi_x for B, psi_x for A), two stages
+  const bool segs = a.pml && t.pw > 0;
+  const MemSeg ms = mem_seg(t.n, segs ? t.pw : 4);
+  float* SEG = WS + ((nw + 3) & ~3);
+  auto segp = [&](int st, int which) { return SEG + (size_t)(st * 2 + which) * ms.floats(); };
+  float* PA = SEG + 4 * ms.floats();  // warm-up partial sums per chunk
+  float* PB = PA + ((t.n + 7) / 8 + 8);
   __syncthreads();
   auto issue = [&](int row, int st) {
     float* S = base + (size_t)st * 6 * RW;
     const int64_t rb = (int64_t)row * t.px;
-    mbar_expect_tx(&bar[st], narr * RB);
+    mbar_expect_tx(&bar[st], narr * RB + (segs ? (a.do_B ? 2u : 1u) * (unsigned)ms.floats() * 4u : 0u));
     bulk_g2s(S, a.v1 + rb, RB, &bar[st]);
     bulk_g2s(S + RW, a.sigma + rb, RB, &bar[st]);
     if (a.do_B) {
@@ -528,6 +580,15 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
       if (KAHAN) bulk_g2s(S + 4 * RW, a.csig + rb, RB, &bar[st]);
     }
     if (KAHAN) bulk_g2s(S + 5 * RW, a.cv1 + rb, RB, &bar[st]);
+    if (segs) {
+      if (a.do_B) {
+        bulk_g2s(segp(st, 0), a.phix + rb, ms.SL * 4u, &bar[st]);
+        bulk_g2s(segp(st, 0) + ms.SL, a.phix + rb + ms.R0, ms.SR * 4u, &bar[st]);
+        if (a.zB.in(row)) prefetch_l2(a.phiz + rb, RB);
+      }
+      bulk_g2s(segp(st, 1), a.psix + rb, ms.SL * 4u, &bar[st]);
+      bulk_g2s(segp(st, 1) + ms.SL, a.psix + rb + ms.R0, ms.SR * 4u, &bar[st]);
+    }
   };
   if (threadIdx.x == 0 && (int)blockIdx.x < nrows) issue(blockIdx.x, 0);
   unsigned parity[2] = {0u, 0u};
@@ -550,7 +611,7 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
     parity[st] ^= 1u;
     float* S = base + (size_t)st * 6 * RW;
     xrow<KAHAN>(a, t, mmagic, row, lay, S, S + RW, S + 2 * RW, S + 3 * RW, S + 4 * RW, S + 5 * RW, base + 12 * RW,
-                rpow, WS, dlf);
+                rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB);
     __syncthreads();
   }
 }
@@ -580,7 +641,11 @@ cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int 
 }
 
 size_t xp_smem(const TileGeom& t) {
-  return (size_t)(2 * 6 + 1) * ((t.n + 1 + 3) & ~3) * 4 + (size_t)(t.p + 1) * (2 * t.Rd + 1) * 4;
+  const int nw = (t.p + 1) * (2 * t.Rd + 1);
+  const int W = t.pw > 0 ? t.pw : 4;
+  const int segf = ((W + 3) & ~3) + ((t.n + 1 - ((t.n + 1 - W) & ~3) + 3) & ~3);
+  return (size_t)(2 * 6 + 1) * ((t.n + 1 + 3) & ~3) * 4 + (size_t)((nw + 3) & ~3) * 4 + (size_t)4 * segf * 4 +
+         (size_t)2 * ((t.n + 7) / 8 + 8) * 4;
 }
 
 template <bool KAHAN>

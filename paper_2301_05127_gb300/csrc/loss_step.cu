@@ -160,6 +160,7 @@ static TileGeom tile_geom(const Shot& s, int k, int* threads) {
   t.inv = (float)fc.inv;
   t.Wd = s.Wd[k];
   t.Rd = std::max(s.d.n_nb, FirLen<float>::K);
+  t.pw = s.pml_on ? s.pml_width : 0;
   t.H = t.Rd;
   if (k == 0) {
     t.ncross = (int)s.len[2];
@@ -193,7 +194,8 @@ static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
 template <bool K>
 static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double amp) {
   const size_t xsm = (size_t)(2 * 6 + 1) * ((s.n[2] + 1 + 3) & ~3) * 4 +
-                     (size_t)(s.p[2] + 1) * (2 * std::max(s.d.n_nb, FirLen<float>::K) + 1) * 4;
+                     (size_t)(s.p[2] + 1) * (2 * std::max(s.d.n_nb, FirLen<float>::K) + 1) * 4 +
+                     (size_t)2 * 2 * (2 * (s.pml_on ? s.pml_width : 0) + 12) * 4 + (size_t)2 * ((s.n[2] + 7) / 8 + 8) * 4;
   if (s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 && xsm + 2048 <= (size_t)h->smem_optin) {
     LOSS_TRY(ensure_delta_weights(h, s, 2));
     int threads;
