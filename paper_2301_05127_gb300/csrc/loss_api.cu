@@ -86,7 +86,7 @@ std::vector<double> pmbc_weights_scaled(int n, int p, int n_nb) {
 // eF_j = a sum_{k=1..K} r^{k-1} (f_{c+k} - f_{c-k}) with the line continued by odd reflection beyond its ends
 // (f_{-q} = 2 f_0 - f_q, f_{n+q} = 2 f_n - f_{n-q}, q clamped to the line).  Formed in FP64; away from the
 // physical ends the two weight sets agree to O(r^K), so the FP32 sum of D f carries no cancellation.
-std::vector<float> fir_delta_weights(int n, int p, int n_nb, int K) {
+std::vector<double> fir_delta_weights(int n, int p, int n_nb, int K) {
   const std::vector<double> W = pmbc_weights_scaled(n, p, n_nb);
   const int M = n / p;
   const int R = std::max(n_nb, K);
@@ -119,7 +119,7 @@ std::vector<float> fir_delta_weights(int n, int p, int n_nb, int K) {
       rk *= r;
     }
   }
-  return std::vector<float>(D.begin(), D.end());
+  return D;
 }
 
 void thomas_tables(std::vector<double>& t64, std::vector<float>& t32) {

@@ -59,6 +59,16 @@ __device__ __forceinline__ T fir_right(const T* __restrict__ f, const BUN& bun, 
   return s;
 }
 
+// FP32 -> FP64 widening on the integer units (IEEE 754: binary32 exponent bias 127, binary64 bias 1023, the 23
+// fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0.
+// Keeps the FP64 pipe, which is narrow on this GPU, free for the FMAs of the junction sums.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return ex ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
+}
+
 // Truncation length: |r|^K below the working precision's rounding (7e-10 for FP32, 1e-16 for FP64).
 template <typename T>
 struct FirLen {

@@ -31,7 +31,7 @@ struct Shot {
   void* model[3] = {};   // acoustic: kappa, b; elastic: lambda, mu, b
   void* tmp[8] = {};     // derivative temporaries (acoustic: tmp[0] = d_z v3)
   double* W[3] = {};     // PMBC weights per axis slot, scaled by h/3
-  float* Wd[3] = {};     // junction-correction weights of the FP32 truncated-convolution kernels (on first use)
+  double* Wd[3] = {};     // junction-correction weights of the FP32 truncated-convolution kernels (on first use)
   bool has_model = false;
   double vmax = 0.0;
   bool b_const = false;  // density constant: buoyancy passed as a scalar, the b array is not read
@@ -157,7 +157,7 @@ loss_status_t run_derivative_adjoint(loss_ctx* h, Shot& s, int k, const void* g,
 loss_status_t run_gradient(loss_ctx* h, Shot& s, const double* d_obs, int32_t checkpoint_every, int64_t n_steps,
                            double* misfit, double* g_vp, double* g_vs, double* g_rho, int32_t mem);
 std::vector<double> pmbc_weights_scaled(int n, int p, int n_nb);
-std::vector<float> fir_delta_weights(int n, int p, int n_nb, int K);
+std::vector<double> fir_delta_weights(int n, int p, int n_nb, int K);
 void thomas_tables(std::vector<double>& t64, std::vector<float>& t32);
 
 // Counts one launch of `kernel` and, when profiling is on, brackets it with CUDA events on the stream.
@@ -219,6 +219,7 @@ template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
                       cudaStream_t st);
 size_t tile_smem_z(const TileGeom& t, int mode);
+size_t xp_smem(const TileGeom& t);
 template <typename T>
 cudaError_t launch_adj(const AdjArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
 template <typename T>

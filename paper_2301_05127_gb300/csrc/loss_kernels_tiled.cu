@@ -34,11 +34,12 @@ __device__ __forceinline__ void fill_rpow(float* rpow, float r) {
   }
 }
 
-// z tiles: junction corrections with the 32 columns on the lanes (conflict-free shared-memory rows).  Items (junction
-// J, tap subset sub), ns = min(8, max(1, warps / 2)) subsets per junction, go round the warps; the partial sums meet
-// in shared memory.  Contains one barrier; dl is ready after the caller's next barrier.
+// z tiles: junction corrections D_j = sum_m Wd[j][m] f_{jM+m}, accumulated in FP64, with the 32 columns on the
+// lanes (conflict-free shared-memory rows).  Items (junction J, tap subset sub), ns = min(8, max(1, warps / 2))
+// subsets per junction, go round the warps; the partial sums meet in shared memory.  Contains one barrier; dl is
+// ready after the caller's next barrier.
 __device__ void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, int nvalid, int jg, const TileGeom& t,
-                                 const float* __restrict__ wsm, float* __restrict__ partf, float* __restrict__ dl) {
+                                 const double* __restrict__ wsm, double* __restrict__ partf, float* __restrict__ dl) {
   const int col = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
@@ -50,18 +51,18 @@ __device__ void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, i
     const int c = j * t.M;
     const int mlo = max(-t.Rd, -c);
     const int mhi = min(t.Rd, t.n - c);
-    const float* wj = wsm + J * wl + t.Rd;
-    float s = 0.0f;
+    const double* wj = wsm + J * wl + t.Rd;
+    double s = 0.0;
     if (col < nvalid)
-      for (int m = mlo + sub; m <= mhi; m += ns) s = fmaf(wj[m], F[bun.at(col, c + m)], s);
+      for (int m = mlo + sub; m <= mhi; m += ns) s = fma(wj[m], widen(F[bun.at(col, c + m)]), s);
     partf[(J * ns + sub) * 32 + col] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 64; i += blockDim.x) {  // (junction, column) pairs; blocks may hold one warp
     const int JJ = i >> 5, cl = i & 31;
-    float s = 0.0f;
+    double s = 0.0;
     for (int q = 0; q < ns; ++q) s += partf[(JJ * ns + q) * 32 + cl];
-    dl[2 * cl + JJ] = s;
+    dl[2 * cl + JJ] = (float)s;
   }
 }
 
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ float rpow[kFirPow];
   __shared__ float dl[64];
-  __shared__ float jpartf[16 * 32];   // junction partial sums [2 x up to 8 subsets][32 columns]
-  __shared__ float wsm[2 * 129];      // the two junctions' correction weights (Rd <= 64)
+  __shared__ double jpart[16 * 32];   // junction partial sums [2 x up to 8 subsets][32 columns]
+  __shared__ double wsm[2 * 129];     // the two junctions' correction weights (Rd <= 64)
   const int l = blockIdx.x % t.p;                  // patch
   const int cg = blockIdx.x / t.p;                 // column group
   const int x0 = cg * 32;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   __syncthreads();
   const ZBun bun{zb};
   const int nvalid = min(32, t.ncross - x0);
-  tile_junctions_z(F, bun, nvalid, l, t, wsm, jpartf, dl);
+  tile_junctions_z(F, bun, nvalid, l, t, wsm, jpart, dl);
   __syncthreads();
   const int col = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;
@@ -284,11 +285,11 @@ __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LA
     if (j < len) e[j] += A * rpow[min(d0 + j, kFirPow - 1)] + B * rpow[min(M - d0 - j, kFirPow - 1)];
 }
 
-// Junction corrections of one row: D_j = sum_m Wd[j][m] f_{jM+m} (FP32; the weights already hold the PMBC sum
-// minus the convolution's own junction value), G lanes per junction.
+// Junction corrections of one row: D_j = sum_m Wd[j][m] f_{jM+m}, accumulated in FP64 (the weights hold the PMBC
+// weights minus the convolution's own junction weights), G lanes per junction.
 template <int G, class BUN>
 __device__ void xf_junctions(const float* __restrict__ row, const BUN& bun, const TileGeom& t,
-                             const float* __restrict__ wd, float* __restrict__ dlf) {
+                             const double* __restrict__ wd, float* __restrict__ dlf) {
   const int g = threadIdx.x % G;
   const int lane = threadIdx.x & 31;
   const unsigned gmask = (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -297,12 +298,12 @@ __device__ void xf_junctions(const float* __restrict__ row, const BUN& bun, cons
     const int c = j * t.M;
     const int mlo = max(-t.Rd, -c);
     const int mhi = min(t.Rd, t.n - c);
-    const float* wj = wd + (size_t)j * wl + t.Rd;
-    float s = 0.0f;
-    for (int m = mlo + g; m <= mhi; m += G) s = fmaf(wj[m], row[bun.at(0, c + m)], s);
+    const double* wj = wd + (size_t)j * wl + t.Rd;
+    double s = 0.0;
+    for (int m = mlo + g; m <= mhi; m += G) s = fma(wj[m], widen(row[bun.at(0, c + m)]), s);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
-    if (g == 0) dlf[j] = s;
+    if (g == 0) dlf[j] = (float)s;
   }
 }
 
@@ -341,7 +342,7 @@ template <bool KAHAN, class LAY>
 __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int row,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
-                                     const float* wd, float* dlf, const MemSeg& ms, const float* segB,
+                                     const double* wd, float* dlf, const MemSeg& ms, const float* segB,
                                      const float* segA, float* PA, float* PB) {
   const int n = t.n, np = n + 1;
   const int M = t.M;
@@ -557,13 +558,13 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
     fence_proxy_async();
   }
   fill_rpow(rpow, t.r);
-  float* WS = base + 13 * RW;  // junction-correction weights, loaded once
+  double* WS = reinterpret_cast<double*>(base + 13 * RW);  // junction-correction weights, loaded once
   const int nw = (t.p + 1) * (2 * t.Rd + 1);
   for (int i = threadIdx.x; i < nw; i += blockDim.x) WS[i] = t.Wd[i];
   // layer segments of the x memory variables (phi_x for B, psi_x for A), two stages
   const bool segs = a.pml && t.pw > 0;
   const MemSeg ms = mem_seg(t.n, segs ? t.pw : 4);
-  float* SEG = WS + ((nw + 3) & ~3);
+  float* SEG = reinterpret_cast<float*>(WS + ((nw + 1) & ~1));
   auto segp = [&](int st, int which) { return SEG + (size_t)(st * 2 + which) * ms.floats(); };
   float* PA = SEG + 4 * ms.floats();  // warm-up partial sums per chunk
   float* PB = PA + ((t.n + 7) / 8 + 8);
@@ -644,7 +645,7 @@ size_t xp_smem(const TileGeom& t) {
   const int nw = (t.p + 1) * (2 * t.Rd + 1);
   const int W = t.pw > 0 ? t.pw : 4;
   const int segf = ((W + 3) & ~3) + ((t.n + 1 - ((t.n + 1 - W) & ~3) + 3) & ~3);
-  return (size_t)(2 * 6 + 1) * ((t.n + 1 + 3) & ~3) * 4 + (size_t)((nw + 3) & ~3) * 4 + (size_t)4 * segf * 4 +
+  return (size_t)(2 * 6 + 1) * ((t.n + 1 + 3) & ~3) * 4 + (size_t)((nw + 1) & ~1) * 8 + (size_t)4 * segf * 4 +
          (size_t)2 * ((t.n + 7) / 8 + 8) * 4;
 }
 

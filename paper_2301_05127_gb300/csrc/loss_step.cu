@@ -179,13 +179,13 @@ static TileGeom tile_geom(const Shot& s, int k, int* threads) {
 // Junction-correction weights of axis slot k in device memory (FP32 truncated-convolution kernels).
 static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
   if (s.Wd[k]) return LOSS_OK;
-  const std::vector<float> D = fir_delta_weights((int)s.n[k], s.p[k], s.d.n_nb, FirLen<float>::K);
+  const std::vector<double> D = fir_delta_weights((int)s.n[k], s.p[k], s.d.n_nb, FirLen<float>::K);
   void* p = nullptr;
-  LOSS_TRY(dev_alloc(h, D.size() * sizeof(float), &p));
-  LOSS_TRY(cuda_check(h, cudaMemcpyAsync(p, D.data(), D.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+  LOSS_TRY(dev_alloc(h, D.size() * sizeof(double), &p));
+  LOSS_TRY(cuda_check(h, cudaMemcpyAsync(p, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream),
                       "copy junction weights"));
   LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
-  s.Wd[k] = (float*)p;
+  s.Wd[k] = (double*)p;
   return LOSS_OK;
 }
 
@@ -193,13 +193,11 @@ static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
 // row fits one block, else the line kernel.
 template <bool K>
 static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double amp) {
-  const size_t xsm = (size_t)(2 * 6 + 1) * ((s.n[2] + 1 + 3) & ~3) * 4 +
-                     (size_t)(s.p[2] + 1) * (2 * std::max(s.d.n_nb, FirLen<float>::K) + 1) * 4 +
-                     (size_t)2 * 2 * (2 * (s.pml_on ? s.pml_width : 0) + 12) * 4 + (size_t)2 * ((s.n[2] + 7) / 8 + 8) * 4;
-  if (s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 && xsm + 2048 <= (size_t)h->smem_optin) {
+  int threads;
+  TileGeom t = tile_geom(s, 2, &threads);
+  if (s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 && xp_smem(t) + 2048 <= (size_t)h->smem_optin) {
     LOSS_TRY(ensure_delta_weights(h, s, 2));
-    int threads;
-    TileGeom t = tile_geom(s, 2, &threads);
+    t.Wd = s.Wd[2];
     t.ncross = (int)s.len[0];
     const unsigned mm = (unsigned)((((uint64_t)1 << 32) + (uint64_t)t.M - 1) / (uint64_t)t.M);
     const AcXArgs<float> a = ac_x_args<float>(h, s, LineGeom{}, do_B, acoef, amp);

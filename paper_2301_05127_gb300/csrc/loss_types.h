@@ -64,7 +64,7 @@ struct TileGeom {
   int n, p, M, n_nb, H, ntl, R, ncross;
   int64_t px;
   const double* W;
-  const float* Wd;   // junction-correction weights [(p + 1)][2 Rd + 1] (PMBC weights minus convolution weights)
+  const double* Wd;  // junction-correction weights [(p + 1)][2 Rd + 1] (PMBC weights minus convolution weights)
   int Rd;            // their half width, max(n_nb, K)
   int pw;            // absorbing-layer width along the axis (0 = no layer)
   float s3h, r, a, rho, inv;
