@@ -35,6 +35,38 @@ UNIT = "pt-upd/s"
 WORKLOAD = "acoustic2d_layered 2049x2049 pts, 8x8 patches (M=256), n_nb=20, PML 40, 3-layer + 5% noise, Ricker 20 Hz"
 
 
+# Source files of the FP32 step's kernels; a DRAM-traffic figure from ncu is valid only for the sources it was taken on.
+KERNEL_SOURCES = ("paper_2301_05127_gb300/csrc/loss_kernels_tiled.cu", "paper_2301_05127_gb300/csrc/loss_fir.cuh",
+                  "paper_2301_05127_gb300/csrc/loss_line.cuh", "paper_2301_05127_gb300/csrc/loss_block.cuh",
+                  "paper_2301_05127_gb300/csrc/loss_types.h")
+KERNEL_OF = {"acoustic_x": "k_xp", "acoustic_z": "k_tz<1", "acoustic_z2": "k_tz<2"}
+
+
+def kernel_sources_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture of the kernel, from
+    profiles/dram_traffic.txt (lines: <kernel> <bytes per launch> <sources digest>), or None when no capture of the
+    current sources exists."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = kernel_sources_digest()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[2] == digest:
+            return float(f[1])
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -294,13 +326,7 @@ def run_ours(args):
     alg = _alg_bytes_per_point(dom, 4, True, False) * pts
     peak, peak_kind = _peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get(dom)
-        except Exception:
-            traffic = None
+    traffic = _traffic(dom)
 
     # accuracy of the timed FP32 run against the FP64 form of the same run (the FP64 form matches the FP64
     # oracle in the parity tests)
