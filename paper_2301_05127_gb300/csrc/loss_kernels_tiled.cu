@@ -322,18 +322,55 @@ __device__ __forceinline__ MemSeg mem_seg(int n, int W) {
   m.SR = (n + 1 - m.R0 + 3) & ~3;
   return m;
 }
-// PmlAxis::step / ::half with the memory value before the sub-step given (same arithmetic).
-__device__ __forceinline__ float pml_step_m0(const PmlAxis<float>& pa, float m0, float* mem, int64_t gi, int i,
-                                             float g) {
-  const int n1 = pa.n + 1;
-  const float m1 = pa.tab[i] * m0 - pa.tab[n1 + i] * g;
+// PmlAxis::step / ::half with the memory value before the sub-step given and the coefficients from a staged table
+// T[4][F] at slot sl (same arithmetic).
+__device__ __forceinline__ float pml_step_s(const float* T, int F, int sl, float m0, float g, float* mem,
+                                            int64_t gi) {
+  const float m1 = T[sl] * m0 - T[F + sl] * g;
   mem[gi] = m1;
-  return pa.tab[2 * n1 + i] * (m1 - m0) - pa.tab[3 * n1 + i] * g;
+  return T[2 * F + sl] * (m1 - m0) - T[3 * F + sl] * g;
 }
-__device__ __forceinline__ float pml_half_m0(const PmlAxis<float>& pa, float m0, int i, float g) {
-  const int n1 = pa.n + 1;
-  const float m1 = pa.tabh[i] * m0 - pa.tabh[n1 + i] * g;
-  return pa.tabh[2 * n1 + i] * (m1 - m0) - pa.tabh[3 * n1 + i] * g;
+__device__ __forceinline__ float pml_half_s(const float* T, int F, int sl, float m0, float g) {
+  const float m1 = T[sl] * m0 - T[F + sl] * g;
+  return T[2 * F + sl] * (m1 - m0) - T[3 * F + sl] * g;
+}
+
+// Chunks of a row that go through the one-point-per-thread pass: the absorbing-layer chunks [0, cL) and [cR, nch)
+// and, on rows of the source block, the chunks [s0, s1] between them that the source touches.  Ordinal k numbers
+// them in that order; their derivative values wait in O[9 k + j].
+struct SlowSet {
+  int cL, cR, nr, s0, s1;  // nr = nch - cR
+  __device__ __forceinline__ int count() const { return cL + nr + (s1 >= s0 ? s1 - s0 + 1 : 0); }
+  __device__ __forceinline__ int chunk(int k) const {
+    return k < cL ? k : (k < cL + nr ? cR + (k - cL) : s0 + (k - cL - nr));
+  }
+  __device__ __forceinline__ int ordinal(int c) const {
+    if (c < cL) return c;
+    if (c >= cR) return cL + (c - cR);
+    return (c >= s0 && c <= s1) ? cL + nr + (c - s0) : -1;
+  }
+};
+// W: layer width (0: no layer); src: the row crosses the source block, whose x extent is xs - 12 .. xs + 12.
+__device__ __forceinline__ SlowSet slow_set(int n, int nch, int W, bool src, int xs) {
+  SlowSet s;
+  if (W > 0) {
+    s.cL = min((W + 7) >> 3, nch);                             // chunks starting before W
+    s.cR = max(min(max(n - W + 1, 0) >> 3, nch - 1), s.cL);  // first chunk reaching past n - W
+  } else {
+    s.cL = 0;
+    s.cR = nch;
+  }
+  s.nr = nch - s.cR;
+  s.s0 = 1;
+  s.s1 = 0;
+  if (src) {  // the last chunk also holds position n
+    const int lo = xs - 12, hi = xs + 12;
+    if (lo <= n) {
+      s.s0 = max(lo < 0 ? 0 : min(lo >> 3, nch - 1), s.cL);
+      s.s1 = min(hi < 0 ? -1 : hi >> 3, s.cR - 1);
+    }
+  }
+  return s;
 }
 
 // One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY).
@@ -343,7 +380,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
                                      const double* wd, float* dlf, const MemSeg& ms, const float* segB,
-                                     const float* segA, float* PA, float* PB) {
+                                     const float* segA, float* PA, float* PB, const float* tabs) {
   const int n = t.n, np = n + 1;
   const int M = t.M;
   const int64_t rb = (int64_t)row * t.px;
@@ -352,18 +389,17 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   const int len = (c == nch - 1) ? np - (c << 3) : 8;
   const int p0 = c << 3;
   const bool act = c < nch;
-  // Points in an absorbing layer or in the source block go through a second pass with one point per thread (their
-  // memory-variable loads are then independent); the chunk pass handles the others in registers.
+  // Points of chunks in an x absorbing layer or in the source block go through a second pass with one point per
+  // thread (its table reads come from shared memory and its memory-variable loads are independent); the chunk pass
+  // handles the others in registers, including the z memory variable of rows in a z layer.
   auto chunk_len = [&](int cc) { return (cc == nch - 1) ? np - (cc << 3) : 8; };
+  const int F = ms.floats();
   if (a.do_B) {
     const double amp = a.src.amp_tab ? a.src.amp_tab[a.src.clk->step] : a.src.amp;
     const bool son = a.src.on && amp != 0.0;
     const bool zlay = a.pml && a.zB.in(row);
     const bool srow = son && (unsigned)(row - a.src.zs + 12) < 25u;
-    auto slowB = [&](int cc) {
-      const int q0 = cc << 3, q1 = q0 + chunk_len(cc) - 1;
-      return zlay || (a.pml && (a.xB.in(q0) || a.xB.in(q1))) || (srow && q1 >= a.src.xs - 12 && q0 <= a.src.xs + 12);
-    };
+    const SlowSet SB = slow_set(n, nch, a.pml ? a.xB.width : 0, srow, a.src.xs);
     if (act) {
       float f8[8];
       lay.eight(V, c, f8);
@@ -374,12 +410,13 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     if (act) {
       float e[9];
       xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
-      if (slowB(c)) {
+      const int ob = SB.ordinal(c);
+      if (ob >= 0) {
 #pragma unroll
         for (int j = 0; j < 9; ++j)
-          if (j < len) O[p0 + j] = t.s3h * e[j];
+          if (j < len) O[9 * ob + j] = t.s3h * e[j];
       } else {
-        float sg[9], cs[9], kp[9], gz[9];
+        float sg[9], cs[9], kp[9], gz[9], iz[9];
         {
           float v8[8];
           lay.eight(D, c, v8);
@@ -402,10 +439,27 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
             if (KAHAN) cs[8] = SC[k8];
           }
         }
+        if (zlay) {  // z memory variable of this row (PmlAxis::step, vectorised)
+          float pz[9];
+          load_run<8>(a.phiz + rb + p0, len, pz);
+          const int n1z = a.zB.n + 1;
+          const float T0 = a.zB.tab[row], T1 = a.zB.tab[n1z + row], T2 = a.zB.tab[2 * n1z + row],
+                      T3 = a.zB.tab[3 * n1z + row];
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            const float m1 = T0 * pz[j] - T1 * gz[j];
+            iz[j] = T2 * (m1 - pz[j]) - T3 * gz[j];
+            pz[j] = m1;
+          }
+          store_run<8>(a.phiz + rb + p0, len, pz);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 9; ++j) iz[j] = -a.dt * gz[j];
+        }
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
           if (j >= len) break;
-          const float delta = kp[j] * (-a.dt * (t.s3h * e[j]) + -a.dt * gz[j]);
+          const float delta = kp[j] * (-a.dt * (t.s3h * e[j]) + iz[j]);
           float v = sg[j];
           if (KAHAN) {
             float cc = cs[j];
@@ -423,13 +477,21 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       }
     }
     __syncthreads();
-    for (int pos = threadIdx.x; pos < np; pos += blockDim.x) {
-      if (!slowB(min(pos >> 3, nch - 1))) continue;
+    const int nsB = 9 * SB.count();
+    for (int q = threadIdx.x; q < nsB; q += blockDim.x) {
+      const int kq = q / 9, j = q - 9 * kq;
+      const int ch = SB.chunk(kq);
+      if (j >= chunk_len(ch)) continue;
+      const int pos = (ch << 3) + j;
       const int64_t gi = rb + pos;
       const int k = lay.bun.at(0, pos);
-      const float gx = O[pos];
+      const float gx = O[q];
       const float gzv = ST[k];
-      const float inc = (a.pml && a.xB.in(pos)) ? pml_step_m0(a.xB, segB[ms.at(pos)], a.phix, gi, pos, gx) : -a.dt * gx;
+      float inc = -a.dt * gx;
+      if (a.pml && a.xB.in(pos)) {
+        const int sl = ms.at(pos);
+        inc = pml_step_s(tabs, F, sl, segB[sl], gx, a.phix, gi);
+      }
       const float incz = zlay ? a.zB.step(a.phiz, gi, row, gzv) : -a.dt * gzv;
       float delta = SK[k] * (inc + incz);
       if (srow) {
@@ -449,10 +511,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     }
     __syncthreads();
   }
-  auto slowA = [&](int cc) {
-    const int q0 = cc << 3, q1 = q0 + chunk_len(cc) - 1;
-    return a.pml && (a.xA.in(q0) || a.xA.in(q1));
-  };
+  const SlowSet SA = slow_set(n, nch, a.pml ? a.xA.width : 0, false, 0);
   if (act) {
     float f8[8];
     lay.eight(D, c, f8);
@@ -463,10 +522,11 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   if (act) {
     float e[9];
     xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
-    if (slowA(c)) {
+    const int oa = SA.ordinal(c);
+    if (oa >= 0) {
 #pragma unroll
       for (int j = 0; j < 9; ++j)
-        if (j < len) O[p0 + j] = t.s3h * e[j];
+        if (j < len) O[9 * oa + j] = t.s3h * e[j];
     } else {
       float vv[9], cs[9], bb[9];
       {
@@ -505,17 +565,22 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     }
   }
   __syncthreads();
-  for (int pos = threadIdx.x; pos < np; pos += blockDim.x) {
-    if (!slowA(min(pos >> 3, nch - 1))) continue;
+  const int nsA = 9 * SA.count();
+  for (int q = threadIdx.x; q < nsA; q += blockDim.x) {
+    const int kq = q / 9, j = q - 9 * kq;
+    const int ch = SA.chunk(kq);
+    if (j >= chunk_len(ch)) continue;
+    const int pos = (ch << 3) + j;
     const int64_t gi = rb + pos;
     const int k = lay.bun.at(0, pos);
-    const float gx = O[pos];
+    const float gx = O[q];
     const float bb = a.b ? a.b[gi] : a.b0;
     float inc;
     if (a.xA.in(pos)) {
-      const float m0 = segA[ms.at(pos)];
-      const float ih = a.dlt ? pml_half_m0(a.xA, m0, pos, gx) : 0.0f;
-      inc = pml_step_m0(a.xA, m0, a.psix, gi, pos, gx);
+      const int sl = ms.at(pos);
+      const float m0 = segA[sl];
+      const float ih = a.dlt ? pml_half_s(tabs + 8 * F, F, sl, m0, gx) : 0.0f;
+      inc = pml_step_s(tabs + 4 * F, F, sl, m0, gx, a.psix, gi);
       if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
     } else {
       inc = -a.acoef * gx;
@@ -531,6 +596,27 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     }
     a.v1[gi] = v;
   }
+}
+
+// Dynamic shared memory of k_xp, in floats: 2 stages x 6 staged rows, the slow chunks' derivative values O, the
+// junction-correction weights (FP64), 2 stages x 2 layer segments of the x memory variables, the warm-up partial
+// sums, and the x layer's coefficient tables (B step, A step, A half step; 4 rows each) at the segment slots.
+struct XpSmem {
+  int RW, O, WS, SEG, PA, TAB, total;
+};
+__host__ __device__ inline XpSmem xp_layout(int n, int p, int Rd, int pw) {
+  XpSmem L;
+  L.RW = (n + 1 + 3) & ~3;
+  const int W = pw > 0 ? pw : 4;
+  const int SL = (W + 3) & ~3, R0 = (n + 1 - W) & ~3, SR = (n + 1 - R0 + 3) & ~3;  // as mem_seg
+  const int nw = (p + 1) * (2 * Rd + 1);
+  L.O = 12 * L.RW;
+  L.WS = L.O + (((2 * ((pw + 7) / 8 + 2) + 5) * 9 + 3) & ~3);
+  L.SEG = L.WS + 2 * ((nw + 1) & ~1);
+  L.PA = L.SEG + 4 * (SL + SR);
+  L.TAB = L.PA + ((2 * ((n + 7) / 8 + 8) + 3) & ~3);
+  L.total = L.TAB + (pw > 0 ? 12 * (SL + SR) : 0);
+  return L;
 }
 
 // Persistent, software-pipelined form: each block takes rows blockIdx.x, blockIdx.x + gridDim.x, ...; one thread
@@ -558,16 +644,31 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
     fence_proxy_async();
   }
   fill_rpow(rpow, t.r);
-  double* WS = reinterpret_cast<double*>(base + 13 * RW);  // junction-correction weights, loaded once
+  const XpSmem L = xp_layout(t.n, t.p, t.Rd, t.pw);
+  double* WS = reinterpret_cast<double*>(base + L.WS);  // junction-correction weights, loaded once
   const int nw = (t.p + 1) * (2 * t.Rd + 1);
   for (int i = threadIdx.x; i < nw; i += blockDim.x) WS[i] = t.Wd[i];
   // layer segments of the x memory variables (phi_x for B, psi_x for A), two stages
   const bool segs = a.pml && t.pw > 0;
   const MemSeg ms = mem_seg(t.n, segs ? t.pw : 4);
-  float* SEG = reinterpret_cast<float*>(WS + ((nw + 1) & ~1));
+  float* SEG = base + L.SEG;
   auto segp = [&](int st, int which) { return SEG + (size_t)(st * 2 + which) * ms.floats(); };
-  float* PA = SEG + 4 * ms.floats();  // warm-up partial sums per chunk
+  float* PA = base + L.PA;  // warm-up partial sums per chunk
   float* PB = PA + ((t.n + 7) / 8 + 8);
+  float* TAB = base + L.TAB;
+  if (segs) {  // x-layer coefficients at the segment slots, loaded once
+    const int F = ms.floats(), n1 = t.n + 1;
+    for (int i = threadIdx.x; i < F; i += blockDim.x) {
+      const int pos = i < ms.SL ? i : ms.R0 + (i - ms.SL);
+      if (pos > t.n) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        TAB[k * F + i] = a.xB.tab[k * n1 + pos];
+        TAB[(4 + k) * F + i] = a.xA.tab[k * n1 + pos];
+        TAB[(8 + k) * F + i] = a.xA.tabh ? a.xA.tabh[k * n1 + pos] : 0.0f;
+      }
+    }
+  }
   __syncthreads();
   auto issue = [&](int row, int st) {
     float* S = base + (size_t)st * 6 * RW;
@@ -611,8 +712,8 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
     }
     parity[st] ^= 1u;
     float* S = base + (size_t)st * 6 * RW;
-    xrow<KAHAN>(a, t, mmagic, row, lay, S, S + RW, S + 2 * RW, S + 3 * RW, S + 4 * RW, S + 5 * RW, base + 12 * RW,
-                rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB);
+    xrow<KAHAN>(a, t, mmagic, row, lay, S, S + RW, S + 2 * RW, S + 3 * RW, S + 4 * RW, S + 5 * RW, base + L.O,
+                rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB);
     __syncthreads();
   }
 }
@@ -641,13 +742,7 @@ cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int 
   return tile_launch(k_tz<2, KAHAN, 4>, grid, threads, smem, st, argv);
 }
 
-size_t xp_smem(const TileGeom& t) {
-  const int nw = (t.p + 1) * (2 * t.Rd + 1);
-  const int W = t.pw > 0 ? t.pw : 4;
-  const int segf = ((W + 3) & ~3) + ((t.n + 1 - ((t.n + 1 - W) & ~3) + 3) & ~3);
-  return (size_t)(2 * 6 + 1) * ((t.n + 1 + 3) & ~3) * 4 + (size_t)((nw + 1) & ~1) * 8 + (size_t)4 * segf * 4 +
-         (size_t)2 * ((t.n + 7) / 8 + 8) * 4;
-}
+size_t xp_smem(const TileGeom& t) { return (size_t)xp_layout(t.n, t.p, t.Rd, t.pw).total * 4; }
 
 template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,

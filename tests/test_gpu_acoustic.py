@@ -172,12 +172,16 @@ def test_velocity_receivers_inside_the_layer(pkg):
     (48, 70, 4, 5, 10, 8),
     (64, 96, 2, 3, 20, 10),
     (80, 48, 1, 1, 24, 8),
+    # sources inside the absorbing layers: at a corner (z and x layers, the line's last chunk) and at the left end
+    (64, 96, 2, 3, 20, 10, (3, 95)),
+    (48, 64, 2, 2, 12, 12, (40, 1)),
 ])
 def test_fp32_kernel_families_on_uneven_geometries(pkg, family, geom):
     """Both kernel families of the FP32 step against the oracle on geometries chosen to reach the edge cases of
     the convolution kernels (tiles of one warp, ragged column groups, patch ends within the truncation length,
     line ends reached by the recursions' warm-up from both sides)."""
-    nz, nx, pz, px, n_nb, layer = geom
+    nz, nx, pz, px, n_nb, layer = geom[:6]
+    src = geom[6] if len(geom) > 6 else (nz // 2, nx // 3)
     w = acoustic2d_small(n=max(nz, nx), p=2, n_nb=n_nb, steps=60, pml_width=layer)
     shape = (nz + 1, nx + 1)
 
@@ -186,7 +190,7 @@ def test_fp32_kernel_families_on_uneven_geometries(pkg, family, geom):
         return np.where(z < nz / 2, 2000.0, 2600.0), None, np.full(shape, 1000.0)
 
     top = np.arange(nx + 1, dtype=np.int64)
-    w = dataclasses.replace(w, n=(nz, nx), p=(pz, px), model_fn=model, src_index=(nz // 2, nx // 3),
+    w = dataclasses.replace(w, n=(nz, nx), p=(pz, px), model_fn=model, src_index=src,
                             receivers={"sigma": top}, f0=60.0, t0=1.2 / 60.0, dt=0.4 * 10.0 / 2600.0)
     errs = _compare(pkg, w, "fp32_kahan", 60, every=20, family=family)
     assert max(errs.values()) < TOL["fp32_kahan"], errs
