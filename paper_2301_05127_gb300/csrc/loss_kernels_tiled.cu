@@ -103,7 +103,7 @@ __device__ __forceinline__ void tile_chunk(const float* __restrict__ F, const BU
 template <int MODE, bool KAHAN, int LOGC>
 __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   constexpr int C = 1 << LOGC;
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float rpow[kFirPow];
   __shared__ float dl[64];
   __shared__ double jpart[16 * 32];   // junction partial sums [2 x up to 8 subsets][32 columns]
@@ -275,14 +275,26 @@ __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LA
       q = fv[j] + r * q;
     }
   // patch corrections: the chunk (and its ninth point, the line's end) lies in one patch since M is a multiple
-  // of 8; r^d is taken as 0 for d >= 63 (r^63 < 1e-36)
+  // of 8; r^d runs along the chunk by multiplication from the table value at its near end (0 beyond the table)
   const int pt = min((int)div_magic(p0, mmagic), t.p - 1);
   const float DL = dlf[pt], DR = dlf[pt + 1];
   const float A = (DL - t.rho * DR) * t.inv, B = (DR - t.rho * DL) * t.inv;
   const int d0 = p0 - pt * M;
+  const int dB = M - d0 - (len - 1);
+  float qa = rpow[min(d0, kFirPow - 1)];  // r^(d0 + j)
+  float qb = rpow[min(dB, kFirPow - 1)];  // r^(M - d0 - j), from j = len - 1 down
 #pragma unroll
   for (int j = 0; j < 9; ++j)
-    if (j < len) e[j] += A * rpow[min(d0 + j, kFirPow - 1)] + B * rpow[min(M - d0 - j, kFirPow - 1)];
+    if (j < len) {
+      e[j] += A * qa;
+      qa *= r;
+    }
+#pragma unroll
+  for (int j = 8; j >= 0; --j)
+    if (j < len) {
+      e[j] += B * qb;
+      qb *= r;
+    }
 }
 
 // Junction corrections of one row: D_j = sum_m Wd[j][m] f_{jM+m}, accumulated in FP64 (the weights hold the PMBC
@@ -405,7 +417,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       lay.eight(V, c, f8);
       xf_partials(f8, t.r, PA[c], PB[c]);
     }
-    xf_junctions<16>(V, lay.bun, t, wd, dlf);
+    xf_junctions<8>(V, lay.bun, t, wd, dlf);
     __syncthreads();
     if (act) {
       float e[9];
@@ -517,7 +529,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     lay.eight(D, c, f8);
     xf_partials(f8, t.r, PA[c], PB[c]);
   }
-  xf_junctions<16>(D, lay.bun, t, wd, dlf);
+  xf_junctions<8>(D, lay.bun, t, wd, dlf);
   __syncthreads();
   if (act) {
     float e[9];
