@@ -84,9 +84,9 @@ struct BatchState {
   int* tile0 = nullptr;   // [2][n_shots + 1]: first tile of each shot, X then Z
   void* jobs = nullptr;   // GatherJob[pre jobs + post jobs]
   StepClock* clk = nullptr;
-  size_t cap_bytes[4] = {};  // allocated bytes of xtab, ztab, tile0, jobs
+  size_t cap_bytes[6] = {};  // allocated bytes of xtab, ztab, tile0, jobs, xptab, tztab
   int clk_cap = 0;
-  std::vector<unsigned char> host[4];  // last uploaded contents of xtab, ztab, tile0, jobs
+  std::vector<unsigned char> host[6];  // last uploaded contents of the same tables
   int xthreads = 0, zthreads = 0, xlogc = 0, zlogc = 0;
   size_t xsmem = 0, zsmem = 0;
   int xtiles = 0, ztiles = 0;
@@ -101,6 +101,15 @@ struct BatchState {
   int64_t graph_k = 0;
   std::vector<int64_t> gsig;
   int64_t graph_launches[LOSS_NUM_KERNELS] = {};  // kernel launches in one replay
+  // FP32 truncated-convolution form: x descriptors, z descriptors of Z1 then Z2; the int table in tile0's slot holds
+  // unit0[n_shots + 1], bunit[xpgrid + 1], bshot[xpgrid], ztile0[n_shots + 1]
+  bool conv = false;
+  void* xptab = nullptr;  // XpShot[n_shots]
+  void* tztab = nullptr;  // TzShot[2 n_shots]
+  XpSmem xl{};
+  int xpthreads = 0, xpgrid = 0, tzthreads = 0, tztiles = 0;
+  int tzgrid[2] = {0, 0};
+  size_t tzsmem[2] = {0, 0};
 };
 
 }  // namespace lossk
@@ -219,7 +228,19 @@ template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
                       cudaStream_t st);
 size_t tile_smem_z(const TileGeom& t, int mode);
-size_t xp_smem(const TileGeom& t);
+size_t xp_smem(const TileGeom& t, bool kahan);
+int xp_rows_per_unit(int n, int threads);
+XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& rs, bool kahan);
+template <bool KAHAN>
+cudaError_t launch_xp_batch(const XpShot* shots, const int* unit0, const int* bunit, const int* bshot,
+                            const XpSmem& L, int threads, int grid, int* err, cudaStream_t st);
+template <bool KAHAN>
+cudaError_t xp_batch_per_sm(const XpSmem& L, int threads, int* per_sm);
+template <bool KAHAN>
+cudaError_t launch_tz_batch(const TzShot* tab, const int* tile0, int nshots, int ntiles, int mode, int threads,
+                            size_t smem, int grid, cudaStream_t st);
+template <bool KAHAN>
+cudaError_t tz_batch_per_sm(int mode, int threads, size_t smem, int* per_sm);
 template <typename T>
 cudaError_t launch_adj(const AdjArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
 template <typename T>

@@ -101,26 +101,6 @@ __device__ __forceinline__ double source_amp(const SourceArgs& s) {
   return s.amp_tab ? s.amp_tab[s.clk->step] : s.amp;
 }
 
-// Shot of tile t in a batched launch: the last s with tile0[s] <= t (tile0 ascending, tile0[0] = 0).
-__device__ __forceinline__ int tile_shot(const int* __restrict__ tile0, int nshots, int t) {
-  int lo = 0, hi = nshots - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile0[mid] <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Block-wide copy of one shot's launch descriptor into shared memory.
-template <class A>
-__device__ __forceinline__ void copy_args(A* dst, const A* __restrict__ src) {
-  static_assert(sizeof(A) % 8 == 0, "descriptor size");
-  const uint64_t* s = reinterpret_cast<const uint64_t*>(src);
-  uint64_t* d = reinterpret_cast<uint64_t*>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(A) / 8); i += blockDim.x) d[i] = s[i];
-}
-
 // X kernel of the 2-D acoustic step: sub-step B on whole x lines, then the x part of sub-step A.  One tile is
 // one bundle `bid` of rows; cc must hold the chunk classes of this geometry.
 template <typename T, int LOGC, bool KAHAN>

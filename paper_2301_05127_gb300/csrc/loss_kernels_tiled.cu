@@ -12,6 +12,9 @@
 // A z tile owns the positions [jM, jM + M) of its patch, and the last patch also the line's last point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "../../include/loss.h"
 #include "loss_block.cuh"
 #include "loss_fir.cuh"
@@ -38,12 +41,15 @@ __device__ __forceinline__ void fill_rpow(float* rpow, float r) {
 // lanes (conflict-free shared-memory rows).  Items (junction J, tap subset sub), ns = min(8, max(1, warps / 2))
 // subsets per junction, go round the warps; the partial sums meet in shared memory.  Contains one barrier; dl is
 // ready after the caller's next barrier.
+// nwj: the warp count that fixes the tap subsets (the single-shot launch's), so that every launch shape sums in the
+// same order.
 __device__ void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, int nvalid, int jg, const TileGeom& t,
-                                 const double* __restrict__ wsm, double* __restrict__ partf, float* __restrict__ dl) {
+                                 int nwj, const double* __restrict__ wsm, double* __restrict__ partf,
+                                 float* __restrict__ dl) {
   const int col = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  const int ns = min(8, max(1, nw >> 1));
+  const int ns = min(8, max(1, nwj >> 1));
   const int wl = 2 * t.Rd + 1;
   for (int it = w; it < 2 * ns; it += nw) {  // item = (junction J, tap subset sub); a lone warp takes both junctions
     const int J = it & 1, sub = it >> 1;
@@ -100,16 +106,21 @@ __device__ __forceinline__ void tile_chunk(const float* __restrict__ F, const BU
 
 // ---------------------------------------------------------------------------------------------------------------
 // z tiles.  MODE 1 (Z1): v3 += b * (z part of A) from d_z sigma.  MODE 2 (Z2): tmp = d_z v3.
+// Shared memory of one tile: the static parts below plus tile_smem_z() dynamic bytes.
+struct TzShared {
+  float rpow[kFirPow];
+  float dl[64];
+  double jpart[16 * 32];  // junction partial sums [2 x up to 8 subsets][32 columns]
+  double wsm[2 * 129];    // the two junctions' correction weights (Rd <= 64)
+};
+// Tile `tile` (patch l = tile % p, column group tile / p) of one shot; nwj as tile_junctions_z.  Ends without a
+// barrier: a caller that reuses the shared memory must synchronise first.
 template <int MODE, bool KAHAN, int LOGC>
-__global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
+__device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom& t, int tile, int nwj,
+                                        unsigned char* sm, TzShared& ts) {
   constexpr int C = 1 << LOGC;
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ float rpow[kFirPow];
-  __shared__ float dl[64];
-  __shared__ double jpart[16 * 32];   // junction partial sums [2 x up to 8 subsets][32 columns]
-  __shared__ double wsm[2 * 129];     // the two junctions' correction weights (Rd <= 64)
-  const int l = blockIdx.x % t.p;                  // patch
-  const int cg = blockIdx.x / t.p;                 // column group
+  const int l = tile % t.p;                        // patch
+  const int cg = tile / t.p;                       // column group
   const int x0 = cg * 32;
   const int z0 = l * t.M;
   const int zb = z0 - t.H;
@@ -119,10 +130,9 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   float* SV = F + rows * 32;                       // MODE 1: v3 of the own rows [M + 1][32]
   float* SC = SV + (t.M + 1) * 32;                 //         compensation of v3
   const float* f = MODE == 1 ? a.sigma : a.v3;
-  fill_rpow(rpow, t.r);
   {
     const int wl = 2 * t.Rd + 1;
-    for (int i = threadIdx.x; i < 2 * wl; i += blockDim.x) wsm[i] = t.Wd[(size_t)l * wl + i];
+    for (int i = threadIdx.x; i < 2 * wl; i += blockDim.x) ts.wsm[i] = t.Wd[(size_t)l * wl + i];
   }
   for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
     const int q = i >> 3, seg = i & 7;
@@ -144,16 +154,17 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   __syncthreads();
   const ZBun bun{zb};
   const int nvalid = min(32, t.ncross - x0);
-  tile_junctions_z(F, bun, nvalid, l, t, wsm, jpart, dl);
+  tile_junctions_z(F, bun, nvalid, l, t, nwj, ts.wsm, ts.jpart, ts.dl);
   __syncthreads();
   const int col = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;
   const int p0 = z0 + c * C;
   int len = min(C, z0 + t.M - p0);
+  if (len <= 0) return;                // warps beyond the patch (a batched block sized for a longer patch)
   if (last && p0 + len == t.n) ++len;  // the line's last point
-  if (col >= nvalid || len <= 0) return;
+  if (col >= nvalid) return;
   float e[C + 1];
-  tile_chunk<C>(F, bun, col, p0, len, z0, t, dl + 2 * col, rpow, e);
+  tile_chunk<C>(F, bun, col, p0, len, z0, t, ts.dl + 2 * col, ts.rpow, e);
   const int64_t base = x0 + col;
 #pragma unroll
   for (int j = 0; j <= C; ++j) {
@@ -185,6 +196,41 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
       v += delta;
     }
     a.v3[gi] = v;
+  }
+}
+
+// One shot: one block per tile, 32 x ceil(M / 16) threads.
+template <int MODE, bool KAHAN, int LOGC>
+__global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ TzShared ts;
+  fill_rpow(ts.rpow, t.r);
+  tz_tile<MODE, KAHAN, LOGC>(a, t, blockIdx.x, blockDim.x >> 5, sm, ts);
+}
+
+// All shots in one persistent launch: tiles tile0[s] .. tile0[s + 1] - 1 belong to shot s; the block size is the
+// largest of the shots' own (at most 512: patches of at most 256 points).
+template <int MODE, bool KAHAN, int LOGC>
+__global__ void __launch_bounds__(512) k_tz_batch(const TzShot* __restrict__ tab, const int* __restrict__ tile0,
+                                                   int nshots, int ntiles) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ TzShared ts;
+  __shared__ __align__(16) unsigned char d_raw[sizeof(TzShot)];
+  __shared__ int s_shot;
+  const TzShot& d = *reinterpret_cast<const TzShot*>(d_raw);
+  int cur = -1;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_shot = tile_shot(tile0, nshots, tile);
+    __syncthreads();
+    const int shot = s_shot;
+    if (shot != cur) {
+      copy_args(reinterpret_cast<TzShot*>(d_raw), tab + shot);
+      __syncthreads();
+      fill_rpow(ts.rpow, d.t.r);
+      cur = shot;
+    }
+    tz_tile<MODE, KAHAN, LOGC>(d.a, d.t, tile - tile0[shot], d.nwj, sm, ts);
+    __syncthreads();
   }
 }
 
@@ -299,14 +345,15 @@ __device__ __forceinline__ void xf_chunk(const float* __restrict__ row, const LA
 
 // Junction corrections of one row: D_j = sum_m Wd[j][m] f_{jM+m}, accumulated in FP64 (the weights hold the PMBC
 // weights minus the convolution's own junction weights), G lanes per junction.
+// tid / nt: the thread's index in its group and the group size (whole warps); a group that is not on skips.
 template <int G, class BUN>
 __device__ void xf_junctions(const float* __restrict__ row, const BUN& bun, const TileGeom& t,
-                             const double* __restrict__ wd, float* __restrict__ dlf) {
-  const int g = threadIdx.x % G;
+                             const double* __restrict__ wd, float* __restrict__ dlf, int tid, int nt, bool on) {
+  const int g = tid % G;
   const int lane = threadIdx.x & 31;
   const unsigned gmask = (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int wl = 2 * t.Rd + 1;
-  for (int j = threadIdx.x / G; j <= t.p; j += blockDim.x / G) {
+  for (int j = on ? tid / G : t.p + 1; j <= t.p; j += nt / G) {
     const int c = j * t.M;
     const int mlo = max(-t.Rd, -c);
     const int mhi = min(t.Rd, t.n - c);
@@ -385,22 +432,24 @@ __device__ __forceinline__ SlowSet slow_set(int n, int nch, int W, bool src, int
   return s;
 }
 
-// One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY).
-// Contains barriers: every thread of the block must call it.
+// One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY),
+// by a group of nt threads (whole warps; tid = index in the group).  Contains block-wide barriers: every thread of
+// the block calls it, each group for its own row (or with on = false: barriers only).
 template <bool KAHAN, class LAY>
 __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int row,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
                                      const double* wd, float* dlf, const MemSeg& ms, const float* segB,
-                                     const float* segA, float* PA, float* PB, const float* tabs) {
+                                     const float* segA, float* PA, float* PB, const float* tabs, int tid, int nt,
+                                     bool on) {
   const int n = t.n, np = n + 1;
   const int M = t.M;
   const int64_t rb = (int64_t)row * t.px;
   const int nch = (n + 7) >> 3;
-  const int c = threadIdx.x;
+  const int c = tid;
   const int len = (c == nch - 1) ? np - (c << 3) : 8;
   const int p0 = c << 3;
-  const bool act = c < nch;
+  const bool act = on && c < nch;
   // Points of chunks in an x absorbing layer or in the source block go through a second pass with one point per
   // thread (its table reads come from shared memory and its memory-variable loads are independent); the chunk pass
   // handles the others in registers, including the z memory variable of rows in a z layer.
@@ -417,7 +466,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       lay.eight(V, c, f8);
       xf_partials(f8, t.r, PA[c], PB[c]);
     }
-    xf_junctions<8>(V, lay.bun, t, wd, dlf);
+    xf_junctions<8>(V, lay.bun, t, wd, dlf, tid, nt, on);
     __syncthreads();
     if (act) {
       float e[9];
@@ -490,7 +539,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     }
     __syncthreads();
     const int nsB = 9 * SB.count();
-    for (int q = threadIdx.x; q < nsB; q += blockDim.x) {
+    for (int q = on ? tid : nsB; q < nsB; q += nt) {
       const int kq = q / 9, j = q - 9 * kq;
       const int ch = SB.chunk(kq);
       if (j >= chunk_len(ch)) continue;
@@ -529,7 +578,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     lay.eight(D, c, f8);
     xf_partials(f8, t.r, PA[c], PB[c]);
   }
-  xf_junctions<8>(D, lay.bun, t, wd, dlf);
+  xf_junctions<8>(D, lay.bun, t, wd, dlf, tid, nt, on);
   __syncthreads();
   if (act) {
     float e[9];
@@ -578,7 +627,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   }
   __syncthreads();
   const int nsA = 9 * SA.count();
-  for (int q = threadIdx.x; q < nsA; q += blockDim.x) {
+  for (int q = on ? tid : nsA; q < nsA; q += nt) {
     const int kq = q / 9, j = q - 9 * kq;
     const int ch = SA.chunk(kq);
     if (j >= chunk_len(ch)) continue;
@@ -610,65 +659,52 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   }
 }
 
-// Dynamic shared memory of k_xp, in floats: 2 stages x 6 staged rows, the slow chunks' derivative values O, the
-// junction-correction weights (FP64), 2 stages x 2 layer segments of the x memory variables, the warm-up partial
-// sums, and the x layer's coefficient tables (B step, A step, A half step; 4 rows each) at the segment slots.
-struct XpSmem {
-  int RW, O, WS, SEG, PA, TAB, total;
+__host__ __device__ inline int xp_mem_floats(int n, int W) {  // MemSeg::floats() of mem_seg(n, W)
+  const int R0 = (n + 1 - W) & ~3;
+  return ((W + 3) & ~3) + ((n + 1 - R0 + 3) & ~3);
+}
+// Sizes in floats of the parts, from which xp_place() builds the offsets.
+struct XpParts {
+  int RW, ocap, ws, F, pa, tab;
 };
-__host__ __device__ inline XpSmem xp_layout(int n, int p, int Rd, int pw) {
+__host__ __device__ inline XpParts xp_parts(int n, int p, int Rd, int pw) {
+  XpParts q;
+  q.RW = (n + 1 + 3) & ~3;
+  q.ocap = ((2 * ((pw + 7) / 8 + 2) + 5) * 9 + 3) & ~3;
+  q.ws = 2 * ((((p + 1) * (2 * Rd + 1)) + 1) & ~1);
+  q.F = xp_mem_floats(n, pw > 0 ? pw : 4);
+  q.pa = (n + 7) / 8 + 8;
+  q.tab = pw > 0 ? 12 * q.F : 0;
+  return q;
+}
+// na: rows staged per stage (6 with compensation arrays, else 4).
+__host__ __device__ inline XpSmem xp_place(const XpParts& q, int na) {
   XpSmem L;
-  L.RW = (n + 1 + 3) & ~3;
-  const int W = pw > 0 ? pw : 4;
-  const int SL = (W + 3) & ~3, R0 = (n + 1 - W) & ~3, SR = (n + 1 - R0 + 3) & ~3;  // as mem_seg
-  const int nw = (p + 1) * (2 * Rd + 1);
-  L.O = 12 * L.RW;
-  L.WS = L.O + (((2 * ((pw + 7) / 8 + 2) + 5) * 9 + 3) & ~3);
-  L.SEG = L.WS + 2 * ((nw + 1) & ~1);
-  L.PA = L.SEG + 4 * (SL + SR);
-  L.TAB = L.PA + ((2 * ((n + 7) / 8 + 8) + 3) & ~3);
-  L.total = L.TAB + (pw > 0 ? 12 * (SL + SR) : 0);
+  L.NA = na;
+  L.DL = 0;
+  L.RW = q.RW;
+  L.O = 2 * na * q.RW;
+  L.WS = L.O + q.ocap;
+  L.SEG = L.WS + q.ws;
+  L.F = q.F;
+  L.PA = L.SEG + 4 * q.F;
+  L.PB = L.PA + q.pa;
+  L.TAB = L.PA + ((2 * q.pa + 3) & ~3);
+  L.total = L.TAB + q.tab;
   return L;
 }
+__host__ __device__ inline XpSmem xp_layout(int n, int p, int Rd, int pw, bool kahan) {
+  return xp_place(xp_parts(n, p, Rd, pw), kahan ? 6 : 4);
+}
 
-// Persistent, software-pipelined form: each block takes rows blockIdx.x, blockIdx.x + gridDim.x, ...; one thread
-// bulk-copies (TMA) the next row's arrays into the other of two shared-memory stages while the block computes the
-// current row, so HBM streams while the block computes.  Waits on the stage barriers are bounded: on a timeout
-// the block records it in *err, waits (bounded) for its copy in flight and stops.
-template <bool KAHAN>
-__global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic, int* err) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ float rpow[kFirPow];
-  __shared__ float dlf[65];
-  __shared__ __align__(8) uint64_t bar[2];
-  const int np = t.n + 1;
-  const int RW = (np + 3) & ~3;           // floats per staged row
-  const unsigned RB = (unsigned)RW * 4u;  // bytes per staged row (multiple of 16)
-  const int nrows = t.ncross;
-  const int G = gridDim.x;
-  const unsigned narr = (a.do_B ? (KAHAN ? 5u : 4u) : 2u) + (KAHAN ? 1u : 0u);
-  const PlainLayout lay{};
-  float* base = reinterpret_cast<float*>(sm);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    fence_proxy_async();
-  }
-  fill_rpow(rpow, t.r);
-  const XpSmem L = xp_layout(t.n, t.p, t.Rd, t.pw);
-  double* WS = reinterpret_cast<double*>(base + L.WS);  // junction-correction weights, loaded once
+// Junction-correction weights (unless WS is null) and x-layer coefficients of one shot into shared memory (no
+// barrier).
+__device__ __forceinline__ void xp_stage_shot(const AcXArgs<float>& a, const TileGeom& t, const MemSeg& ms, bool segs,
+                                              double* WS, float* TAB) {
   const int nw = (t.p + 1) * (2 * t.Rd + 1);
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) WS[i] = t.Wd[i];
-  // layer segments of the x memory variables (phi_x for B, psi_x for A), two stages
-  const bool segs = a.pml && t.pw > 0;
-  const MemSeg ms = mem_seg(t.n, segs ? t.pw : 4);
-  float* SEG = base + L.SEG;
-  auto segp = [&](int st, int which) { return SEG + (size_t)(st * 2 + which) * ms.floats(); };
-  float* PA = base + L.PA;  // warm-up partial sums per chunk
-  float* PB = PA + ((t.n + 7) / 8 + 8);
-  float* TAB = base + L.TAB;
-  if (segs) {  // x-layer coefficients at the segment slots, loaded once
+  if (WS)
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) WS[i] = t.Wd[i];
+  if (segs) {
     const int F = ms.floats(), n1 = t.n + 1;
     for (int i = threadIdx.x; i < F; i += blockDim.x) {
       const int pos = i < ms.SL ? i : ms.R0 + (i - ms.SL);
@@ -681,28 +717,82 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
       }
     }
   }
+}
+
+// Bytes that xp_issue copies for one row.
+template <bool KAHAN>
+__device__ __forceinline__ unsigned xp_row_bytes(const AcXArgs<float>& a, const TileGeom& t, const MemSeg& ms,
+                                                 bool segs) {
+  const unsigned RB = (unsigned)((t.n + 1 + 3) & ~3) * 4u;
+  const unsigned narr = (a.do_B ? (KAHAN ? 5u : 4u) : 2u) + (KAHAN ? 1u : 0u);
+  return narr * RB + (segs ? (a.do_B ? 2u : 1u) * (unsigned)ms.floats() * 4u : 0u);
+}
+// Bulk copies (one thread) of row `row` of one shot into a stage: six rows at S + k * stride and the two layer
+// segments, completing on *bar (whose expected bytes the caller has raised by xp_row_bytes).
+template <bool KAHAN>
+__device__ __forceinline__ void xp_issue(const AcXArgs<float>& a, const TileGeom& t, const MemSeg& ms, bool segs,
+                                         int row, float* S, int stride, float* seg0, float* seg1, uint64_t* bar) {
+  const int RW = (t.n + 1 + 3) & ~3;
+  const unsigned RB = (unsigned)RW * 4u;
+  const int64_t rb = (int64_t)row * t.px;
+  bulk_g2s(S, a.v1 + rb, RB, bar);
+  bulk_g2s(S + stride, a.sigma + rb, RB, bar);
+  if (a.do_B) {
+    bulk_g2s(S + 2 * stride, a.kappa + rb, RB, bar);
+    bulk_g2s(S + 3 * stride, a.tmp + rb, RB, bar);
+    if (KAHAN) bulk_g2s(S + 4 * stride, a.csig + rb, RB, bar);
+  }
+  if (KAHAN) bulk_g2s(S + 5 * stride, a.cv1 + rb, RB, bar);
+  if (segs) {
+    if (a.do_B) {
+      bulk_g2s(seg0, a.phix + rb, ms.SL * 4u, bar);
+      bulk_g2s(seg0 + ms.SL, a.phix + rb + ms.R0, ms.SR * 4u, bar);
+      if (a.zB.in(row)) prefetch_l2(a.phiz + rb, RB);
+    }
+    bulk_g2s(seg1, a.psix + rb, ms.SL * 4u, bar);
+    bulk_g2s(seg1 + ms.SL, a.psix + rb + ms.R0, ms.SR * 4u, bar);
+  }
+}
+
+__device__ __forceinline__ void xp_init_barriers(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_proxy_async();
+  }
+}
+
+// Persistent, software-pipelined form: each block takes rows blockIdx.x, blockIdx.x + gridDim.x, ...; one thread
+// bulk-copies (TMA) the next row's arrays into the other of two shared-memory stages while the block computes the
+// current row, so HBM streams while the block computes.  Waits on the stage barriers are bounded: on a timeout
+// the block records it in *err, waits (bounded) for its copy in flight and stops.
+template <bool KAHAN>
+__global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic, int* err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ float rpow[kFirPow];
+  __shared__ float dlf[65];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int nrows = t.ncross;
+  const int G = gridDim.x;
+  const PlainLayout lay{};
+  float* base = reinterpret_cast<float*>(sm);
+  xp_init_barriers(bar);
+  fill_rpow(rpow, t.r);
+  const XpSmem L = xp_layout(t.n, t.p, t.Rd, t.pw, KAHAN);
+  double* WS = reinterpret_cast<double*>(base + L.WS);
+  const bool segs = a.pml && t.pw > 0;
+  const MemSeg ms = mem_seg(t.n, segs ? t.pw : 4);
+  float* SEG = base + L.SEG;
+  auto segp = [&](int st, int which) { return SEG + (size_t)(st * 2 + which) * L.F; };
+  float* PA = base + L.PA;  // warm-up partial sums per chunk
+  float* PB = base + L.PB;
+  float* TAB = base + L.TAB;
+  xp_stage_shot(a, t, ms, segs, WS, TAB);  // loaded once
   __syncthreads();
   auto issue = [&](int row, int st) {
-    float* S = base + (size_t)st * 6 * RW;
-    const int64_t rb = (int64_t)row * t.px;
-    mbar_expect_tx(&bar[st], narr * RB + (segs ? (a.do_B ? 2u : 1u) * (unsigned)ms.floats() * 4u : 0u));
-    bulk_g2s(S, a.v1 + rb, RB, &bar[st]);
-    bulk_g2s(S + RW, a.sigma + rb, RB, &bar[st]);
-    if (a.do_B) {
-      bulk_g2s(S + 2 * RW, a.kappa + rb, RB, &bar[st]);
-      bulk_g2s(S + 3 * RW, a.tmp + rb, RB, &bar[st]);
-      if (KAHAN) bulk_g2s(S + 4 * RW, a.csig + rb, RB, &bar[st]);
-    }
-    if (KAHAN) bulk_g2s(S + 5 * RW, a.cv1 + rb, RB, &bar[st]);
-    if (segs) {
-      if (a.do_B) {
-        bulk_g2s(segp(st, 0), a.phix + rb, ms.SL * 4u, &bar[st]);
-        bulk_g2s(segp(st, 0) + ms.SL, a.phix + rb + ms.R0, ms.SR * 4u, &bar[st]);
-        if (a.zB.in(row)) prefetch_l2(a.phiz + rb, RB);
-      }
-      bulk_g2s(segp(st, 1), a.psix + rb, ms.SL * 4u, &bar[st]);
-      bulk_g2s(segp(st, 1) + ms.SL, a.psix + rb + ms.R0, ms.SR * 4u, &bar[st]);
-    }
+    mbar_expect_tx(&bar[st], xp_row_bytes<KAHAN>(a, t, ms, segs));
+    xp_issue<KAHAN>(a, t, ms, segs, row, base + (size_t)st * L.NA * L.RW, L.RW, segp(st, 0), segp(st, 1), &bar[st]);
   };
   if (threadIdx.x == 0 && (int)blockIdx.x < nrows) issue(blockIdx.x, 0);
   unsigned parity[2] = {0u, 0u};
@@ -723,9 +813,124 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
       return;
     }
     parity[st] ^= 1u;
-    float* S = base + (size_t)st * 6 * RW;
-    xrow<KAHAN>(a, t, mmagic, row, lay, S, S + RW, S + 2 * RW, S + 3 * RW, S + 4 * RW, S + 5 * RW, base + L.O,
-                rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB);
+    float* S = base + (size_t)st * L.NA * L.RW;
+    xrow<KAHAN>(a, t, mmagic, row, lay, S, S + L.RW, S + 2 * L.RW, S + 3 * L.RW, S + 4 * L.RW, S + 5 * L.RW,
+                base + L.O, rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB, threadIdx.x, blockDim.x, true);
+    __syncthreads();
+  }
+}
+
+// All shots in one persistent launch.  Work comes in units of R consecutive rows of one shot (R = XpShot::R, the
+// rows that R groups of blockDim / R threads compute side by side, so that short rows fill the block); the units
+// of shot s are unit0[s] .. unit0[s + 1] - 1, and block b takes the units bunit[b] .. bunit[b + 1] - 1 (about the
+// same number of points per block), the first of them in shot bshot[b].  The pipeline is that of k_xp; a stage
+// records the shot of its unit, the descriptors of the (at most two) live shots sit in two slots (shot s in slot
+// s & 1), and a block restages the weights and layer tables when its units move on to the next shot.  Shared
+// memory of a stage: array k of group g at S + k * RR + g * RW (RR = R * RW); per group its own O, warm-up sums,
+// layer segments and junction corrections.
+template <bool KAHAN>
+__global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ shots, const int* __restrict__ unit0,
+                                                     const int* __restrict__ bunit, const int* __restrict__ bshot,
+                                                     XpSmem L, int* err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ float rpow[kFirPow];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) unsigned char slot[2][sizeof(XpShot)];
+  __shared__ int stage_shot[2];
+  const int u0 = bunit[blockIdx.x], u1 = bunit[blockIdx.x + 1];
+  if (u0 >= u1) return;
+  const PlainLayout lay{};
+  float* base = reinterpret_cast<float*>(sm);
+  xp_init_barriers(bar);
+  float* TAB = base + L.TAB;
+  float* dlf = base + L.DL;  // junction corrections, 65 per group
+  auto desc = [&](int s) -> const XpShot& { return *reinterpret_cast<const XpShot*>(slot[s & 1]); };
+  // per-shot geometry of the stage and group regions
+  struct Geo {
+    int R, RW, RR, F, ocap, pa;
+  };
+  auto geo = [&](const XpShot& d) {
+    Geo q;
+    q.R = d.R;
+    q.RW = (d.t.n + 1 + 3) & ~3;
+    q.RR = q.R * q.RW;
+    q.F = xp_mem_floats(d.t.n, (d.a.pml && d.t.pw > 0) ? d.t.pw : 4);
+    q.ocap = ((2 * ((d.t.pw + 7) / 8 + 2) + 5) * 9 + 3) & ~3;
+    q.pa = (d.t.n + 7) / 8 + 8;
+    return q;
+  };
+  auto segp = [&](int st, int which, const Geo& q, int g) {
+    return base + L.SEG + (size_t)(st * 2 + which) * L.F + (size_t)g * q.F;
+  };
+  // thread 0's view of the shot of the units it issues
+  int is = bshot[blockIdx.x];
+  int iend = 0;
+  auto load_desc = [&](int s) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(shots + s);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(slot[s & 1]);
+    for (int w = 0; w < (int)(sizeof(XpShot) / 8); ++w) dst[w] = src[w];
+  };
+  if (threadIdx.x == 0) {
+    load_desc(is);
+    iend = unit0[is + 1];
+  }
+  fill_rpow(rpow, shots[is].t.r);
+  auto issue = [&](int u, int st) {  // thread 0
+    while (u >= iend) {
+      ++is;
+      load_desc(is);
+      iend = unit0[is + 1];
+    }
+    stage_shot[st] = is;
+    const XpShot& d = desc(is);
+    const Geo q = geo(d);
+    const bool segs = d.a.pml && d.t.pw > 0;
+    const MemSeg ms = mem_seg(d.t.n, segs ? d.t.pw : 4);
+    const int r0 = (u - d.unit0) * q.R;
+    const int nr = min(q.R, d.t.ncross - r0);
+    mbar_expect_tx(&bar[st], (unsigned)nr * xp_row_bytes<KAHAN>(d.a, d.t, ms, segs));
+    for (int g = 0; g < nr; ++g)
+      xp_issue<KAHAN>(d.a, d.t, ms, segs, r0 + g, base + (size_t)st * L.NA * L.RW + (size_t)g * q.RW, q.RR,
+                      segp(st, 0, q, g), segp(st, 1, q, g), &bar[st]);
+  };
+  if (threadIdx.x == 0) issue(u0, 0);
+  unsigned parity[2] = {0u, 0u};
+  int loaded = -1;
+  int i = 0;
+  for (int u = u0; u < u1; ++u, ++i) {
+    const int st = i & 1;
+    const bool more = u + 1 < u1;
+    if (threadIdx.x == 0 && more) {
+      fence_proxy_async();
+      issue(u + 1, st ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[st], parity[st], 1u << 24);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], 1u << 24);
+      }
+      return;
+    }
+    parity[st] ^= 1u;
+    const int s = stage_shot[st];
+    const XpShot& d = desc(s);
+    const Geo q = geo(d);
+    const bool segs = d.a.pml && d.t.pw > 0;
+    const MemSeg ms = mem_seg(d.t.n, segs ? d.t.pw : 4);
+    if (s != loaded) {  // the junction weights are read from global memory (L1) here, not staged
+      xp_stage_shot(d.a, d.t, ms, segs, nullptr, TAB);
+      loaded = s;
+      __syncthreads();
+    }
+    const int nt = blockDim.x / q.R;
+    const int g = threadIdx.x / nt;
+    const int row = (u - d.unit0) * q.R + g;
+    float* S = base + (size_t)st * L.NA * L.RW + (size_t)g * q.RW;
+    float* PAg = base + L.PA + (size_t)g * 2 * q.pa;
+    xrow<KAHAN>(d.a, d.t, d.mmagic, row, lay, S, S + q.RR, S + 2 * q.RR, S + 3 * q.RR, S + 4 * q.RR, S + 5 * q.RR,
+                base + L.O + (size_t)g * q.ocap, rpow, d.t.Wd, dlf + g * 65, ms, segp(st, 0, q, g), segp(st, 1, q, g),
+                PAg, PAg + q.pa, TAB, threadIdx.x - g * nt, nt, row < d.t.ncross);
     __syncthreads();
   }
 }
@@ -754,7 +959,85 @@ cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int 
   return tile_launch(k_tz<2, KAHAN, 4>, grid, threads, smem, st, argv);
 }
 
-size_t xp_smem(const TileGeom& t) { return (size_t)xp_layout(t.n, t.p, t.Rd, t.pw).total * 4; }
+size_t xp_smem(const TileGeom& t, bool kahan) { return (size_t)xp_layout(t.n, t.p, t.Rd, t.pw, kahan).total * 4; }
+
+// Rows per work unit of a batched x launch of `threads` threads: as many groups of whole warps as the row's
+// chunks leave room for, at most kXpMaxGroups.
+int xp_rows_per_unit(int n, int threads) {
+  const int need = 32 * (((n + 7) / 8 + 31) / 32);
+  int R = 1;
+  while (R < kXpMaxGroups && 2 * R * need <= threads && (threads / (2 * R)) % 32 == 0) R *= 2;
+  return R;
+}
+
+// Layout of a batched x launch: every part as large as the largest shot's, the per-group parts times the shot's
+// rows per unit R (rs[i]); no staged weights, and the junction corrections of the groups after the tables.
+XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& rs, bool kahan) {
+  int RW = 0, ocap = 0, F = 0, pa = 0, tab = 0, R = 1;
+  for (size_t i = 0; i < ts.size(); ++i) {
+    const TileGeom& t = ts[i];
+    const XpParts q = xp_parts(t.n, t.p, t.Rd, t.pw);
+    RW = std::max(RW, rs[i] * q.RW);
+    ocap = std::max(ocap, rs[i] * q.ocap);
+    F = std::max(F, rs[i] * q.F);
+    pa = std::max(pa, rs[i] * 2 * q.pa);
+    tab = std::max(tab, 12 * q.F);
+    R = std::max(R, rs[i]);
+  }
+  XpSmem L;
+  L.NA = kahan ? 6 : 4;
+  L.RW = (RW + 3) & ~3;
+  L.O = 2 * L.NA * L.RW;
+  L.WS = L.O + ((ocap + 3) & ~3);
+  L.SEG = L.WS;
+  L.F = (F + 3) & ~3;
+  L.PA = L.SEG + 4 * L.F;
+  L.PB = L.PA;  // per group: PA at 2 g pa, PB at 2 g pa + pa
+  L.TAB = L.PA + ((pa + 3) & ~3);
+  L.DL = L.TAB + ((tab + 3) & ~3);
+  L.total = L.DL + ((R * 65 + 3) & ~3);
+  return L;
+}
+
+template <bool KAHAN>
+cudaError_t launch_xp_batch(const XpShot* shots, const int* unit0, const int* bunit, const int* bshot,
+                            const XpSmem& L, int threads, int grid, int* err, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  XpSmem l = L;
+  void* argv[] = {(void*)&shots, (void*)&unit0, (void*)&bunit, (void*)&bshot, (void*)&l, (void*)&err};
+  return tile_launch(k_xp_batch<KAHAN>, grid, threads, (size_t)L.total * 4, st, argv);
+}
+template <bool KAHAN>
+cudaError_t xp_batch_per_sm(const XpSmem& L, int threads, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_xp_batch<KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total * 4);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_xp_batch<KAHAN>, threads, (size_t)L.total * 4);
+}
+template <bool KAHAN>
+cudaError_t launch_tz_batch(const TzShot* tab, const int* tile0, int nshots, int ntiles, int mode, int threads,
+                            size_t smem, int grid, cudaStream_t st) {
+  if (grid <= 0 || ntiles <= 0) return cudaSuccess;
+  void* argv[] = {(void*)&tab, (void*)&tile0, (void*)&nshots, (void*)&ntiles};
+  if (mode == 1) return tile_launch(k_tz_batch<1, KAHAN, 4>, grid, threads, smem, st, argv);
+  return tile_launch(k_tz_batch<2, KAHAN, 4>, grid, threads, smem, st, argv);
+}
+template <bool KAHAN>
+cudaError_t tz_batch_per_sm(int mode, int threads, size_t smem, int* per_sm) {
+  auto kern = mode == 1 ? k_tz_batch<1, KAHAN, 4> : k_tz_batch<2, KAHAN, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
+}
+template cudaError_t launch_xp_batch<false>(const XpShot*, const int*, const int*, const int*, const XpSmem&, int, int,
+                                            int*, cudaStream_t);
+template cudaError_t launch_xp_batch<true>(const XpShot*, const int*, const int*, const int*, const XpSmem&, int, int,
+                                           int*, cudaStream_t);
+template cudaError_t xp_batch_per_sm<false>(const XpSmem&, int, int*);
+template cudaError_t xp_batch_per_sm<true>(const XpSmem&, int, int*);
+template cudaError_t launch_tz_batch<false>(const TzShot*, const int*, int, int, int, int, size_t, int, cudaStream_t);
+template cudaError_t launch_tz_batch<true>(const TzShot*, const int*, int, int, int, int, size_t, int, cudaStream_t);
+template cudaError_t tz_batch_per_sm<false>(int, int, size_t, int*);
+template cudaError_t tz_batch_per_sm<true>(int, int, size_t, int*);
 
 template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
@@ -766,7 +1049,7 @@ cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagi
   void* argv[] = {&aa, &tt, &mm, &e};
   const int threads = (((t.n + 7) / 8 + 31) / 32) * 32;
   const int grid = t.ncross < 2 * num_sms ? t.ncross : 2 * num_sms;
-  return tile_launch(k_xp<KAHAN>, grid, threads, xp_smem(t), st, argv);
+  return tile_launch(k_xp<KAHAN>, grid, threads, xp_smem(t, KAHAN), st, argv);
 }
 template cudaError_t launch_xp<false>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);
 template cudaError_t launch_xp<true>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);

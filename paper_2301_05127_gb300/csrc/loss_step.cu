@@ -189,13 +189,20 @@ static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
   return LOSS_OK;
 }
 
+// The pipelined x kernel takes rows of at most 2048 points in at most 64 patches whose length is a multiple of 8,
+// with the staged rows within shared memory.
+static bool xp_ok(const loss_ctx* h, const Shot& s, const TileGeom& t) {
+  return s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 &&
+         xp_smem(t, s.kahan) + 2048 <= (size_t)h->smem_optin;
+}
+
 // x part of the FP32 step (sub-step B and the x part of A, or the latter alone): the pipelined row kernel when a
 // row fits one block, else the line kernel.
 template <bool K>
 static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double amp) {
   int threads;
   TileGeom t = tile_geom(s, 2, &threads);
-  if (s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 && xp_smem(t) + 2048 <= (size_t)h->smem_optin) {
+  if (xp_ok(h, s, t)) {
     LOSS_TRY(ensure_delta_weights(h, s, 2));
     t.Wd = s.Wd[2];
     t.ncross = (int)s.len[0];
@@ -528,6 +535,33 @@ static loss_status_t batch_launch_step(loss_ctx* h) {
     LaunchScope ls(h, LOSS_KERNEL_GATHER);
     LOSS_TRY(cuda_check(h, launch_gather_batch<T>(jobs, B.npre, B.pre_max, h->stream), "batched receiver gather"));
   }
+  if constexpr (sizeof(T) == 4) {
+    if (B.conv) {
+      const int* unit0 = B.tile0;
+      const int* bunit = unit0 + S + 1;
+      const int* bshot = bunit + B.xpgrid + 1;
+      const int* zt0 = bshot + B.xpgrid;
+      {
+        LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
+        LOSS_TRY(cuda_check(h, launch_xp_batch<K>((const XpShot*)B.xptab, unit0, bunit, bshot, B.xl, B.xpthreads,
+                                                  B.xpgrid, h->dflag, h->stream),
+                            "batched acoustic x kernel"));
+      }
+      for (int mode = 1; mode <= 2; ++mode) {
+        LaunchScope ls(h, mode == 1 ? LOSS_KERNEL_ACOUSTIC_Z : LOSS_KERNEL_ACOUSTIC_Z2);
+        LOSS_TRY(cuda_check(h, launch_tz_batch<K>((const TzShot*)B.tztab + (mode - 1) * S, zt0, S, B.tztiles, mode,
+                                                  B.tzthreads, B.tzsmem[mode - 1], B.tzgrid[mode - 1], h->stream),
+                            "batched acoustic z tile kernel"));
+      }
+      if (B.npost) {
+        LaunchScope ls(h, LOSS_KERNEL_GATHER);
+        LOSS_TRY(cuda_check(h, launch_gather_batch<T>(jobs + B.npre, B.npost, B.post_max, h->stream),
+                            "batched receiver gather"));
+      }
+      LaunchScope ls(h, LOSS_KERNEL_CLOCK);
+      return cuda_check(h, launch_tick(B.clk, S, h->stream), "clock tick");
+    }
+  }
   {
     LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
     LOSS_TRY(cuda_check(h, launch_ac_x_batch<T, K>((const AcXArgs<T>*)B.xtab, B.tile0, S, B.xtiles, B.xlogc,
@@ -588,24 +622,147 @@ static loss_status_t capture_graph(loss_ctx* h, int64_t k) {
   return LOSS_OK;
 }
 
+// Every shot takes the FP32 truncated-convolution kernels (z tiles of patches of at most 256 points and the
+// pipelined x kernel), and their batched x layout fits shared memory.
+static bool conv_batch_ok(const loss_ctx* h) {
+  std::vector<TileGeom> ts;
+  int threads = 32;
+  for (const Shot& s : h->shots) {
+    if (!tiled_ok(h, s) || s.n[0] / s.p[0] > 256) return false;
+    int thr;
+    TileGeom t = tile_geom(s, 2, &thr);
+    if (!xp_ok(h, s, t)) return false;
+    ts.push_back(t);
+    threads = std::max(threads, thr);
+  }
+  std::vector<int> rs;
+  for (const TileGeom& t : ts) rs.push_back(xp_rows_per_unit(t.n, threads));
+  return !ts.empty() &&
+         (size_t)xp_batch_layout(ts, rs, h->shots[0].kahan).total * 4 + 2048 <= (size_t)h->smem_optin;
+}
+
+// Descriptors, work ranges and launch shapes of the batched convolution kernels (the shots are staggered and their
+// amplitude tables exist).  The x blocks take whole units of rows in about equal numbers of points.
+template <bool K>
+static loss_status_t conv_tables(loss_ctx* h) {
+  BatchState& B = h->batch;
+  const int S = (int)h->shots.size();
+  std::vector<XpShot> xs(S);
+  std::vector<TzShot> zs(2 * S);
+  std::vector<TileGeom> txs(S);
+  std::vector<int> unit0(S + 1, 0), zt0(S + 1, 0), rs(S);
+  int xthreads = 32, zthreads = 32;
+  size_t zsm[2] = {0, 0};
+  int64_t ptot = 0;
+  for (int i = 0; i < S; ++i) {
+    int thr;
+    tile_geom(h->shots[i], 2, &thr);
+    xthreads = std::max(xthreads, thr);
+  }
+  for (int i = 0; i < S; ++i) {
+    Shot& s = h->shots[i];
+    LOSS_TRY(ensure_delta_weights(h, s, 0));
+    LOSS_TRY(ensure_delta_weights(h, s, 2));
+    int thr;
+    TileGeom tx = tile_geom(s, 2, &thr);
+    tx.ncross = (int)s.len[0];
+    XpShot& x = xs[i];
+    x.a = ac_x_args<float>(h, s, LineGeom{}, 1, s.d.dt, 0.0);
+    x.a.src.on = (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE)) ? 1 : 0;
+    x.a.src.amp_tab = s.amp_tab;
+    x.a.src.clk = B.clk + i;
+    x.t = tx;
+    x.mmagic = (unsigned)((((uint64_t)1 << 32) + (uint64_t)tx.M - 1) / (uint64_t)tx.M);
+    rs[i] = xp_rows_per_unit(tx.n, xthreads);
+    x.R = rs[i];
+    x.unit0 = unit0[i];
+    x.pad = 0;
+    unit0[i + 1] = unit0[i] + (tx.ncross + rs[i] - 1) / rs[i];
+    ptot += (int64_t)(tx.n + 1) * tx.ncross;
+    txs[i] = tx;
+    const TileGeom tz = tile_geom(s, 0, &thr);
+    zs[i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, s.d.dt, 0), tz, thr >> 5, 0};
+    zs[S + i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, 0.0, 0), tz, thr >> 5, 0};
+    zthreads = std::max(zthreads, thr);
+    zsm[0] = std::max(zsm[0], tile_smem_z(tz, 1));
+    zsm[1] = std::max(zsm[1], tile_smem_z(tz, 2));
+    zt0[i + 1] = zt0[i] + tz.ntl * tz.p;
+  }
+  B.xl = xp_batch_layout(txs, rs, K);
+  B.xpthreads = xthreads;
+  int per = 0;
+  LOSS_TRY(cuda_check(h, xp_batch_per_sm<K>(B.xl, xthreads, &per), "batched x kernel shape"));
+  if (per < 1) {
+    h->err = "batched x kernel does not fit an SM";
+    return LOSS_E_UNSUPPORTED;
+  }
+  const int G = (int)std::min<int64_t>(unit0[S], (int64_t)per * h->num_sms);
+  // block b starts at the first unit whose preceding points reach b * ptot / G
+  std::vector<int> brow(G + 1, unit0[S]), bshot(G, S - 1);
+  {
+    int b = 0, u = 0;
+    int64_t before = 0;
+    for (int i = 0; i < S && b < G; ++i)
+      for (int w = 0; w < unit0[i + 1] - unit0[i] && b < G; ++w, ++u) {
+        while (b < G && before >= (ptot * b + G - 1) / G) {
+          brow[b] = u;
+          bshot[b] = i;
+          ++b;
+        }
+        before += (int64_t)(txs[i].n + 1) * std::min(rs[i], txs[i].ncross - w * rs[i]);
+      }
+  }
+  B.xpgrid = G;
+  B.tzthreads = zthreads;
+  B.tztiles = zt0[S];
+  for (int m = 0; m < 2; ++m) {
+    B.tzsmem[m] = zsm[m];
+    LOSS_TRY(cuda_check(h, tz_batch_per_sm<K>(m + 1, zthreads, zsm[m], &per), "batched z kernel shape"));
+    if (per < 1) {
+      h->err = "batched z kernel does not fit an SM";
+      return LOSS_E_UNSUPPORTED;
+    }
+    B.tzgrid[m] = std::min(B.tztiles, per * h->num_sms);
+  }
+  std::vector<int> ints = unit0;
+  ints.insert(ints.end(), brow.begin(), brow.end());
+  ints.insert(ints.end(), bshot.begin(), bshot.end());
+  ints.insert(ints.end(), zt0.begin(), zt0.end());
+  LOSS_TRY(upload_table(h, 4, as_bytes(xs), &B.xptab));
+  LOSS_TRY(upload_table(h, 5, as_bytes(zs), &B.tztab));
+  void* t0p = B.tile0;
+  LOSS_TRY(upload_table(h, 2, as_bytes(ints), &t0p));
+  B.tile0 = (int*)t0p;
+  return LOSS_OK;
+}
+
 template <typename T, bool K>
 static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
   BatchState& B = h->batch;
   const int S = (int)h->shots.size();
-  // per-shot preparation: receiver corrections, staggered start, source amplitudes
+  B.conv = false;
+  if constexpr (sizeof(T) == 4) B.conv = conv_batch_ok(h);
+  // per-shot preparation: receiver corrections, staggered start (that of the per-shot schedule of the same
+  // kernels), source amplitudes
   for (Shot& s : h->shots) {
     LOSS_TRY(ensure_rdelta(h, s));
     if (!s.staggered) {
-      LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * s.d.dt, 0.0)));
-      LOSS_TRY((ac_z<T, K>(h, s, 0.5 * s.d.dt, 1)));
+      if (B.conv) {
+        LOSS_TRY((acoustic2d_start<T, K>(h, s)));
+      } else {
+        LOSS_TRY((ac_x<T, K>(h, s, 0, 0.5 * s.d.dt, 0.0)));
+        LOSS_TRY((ac_z<T, K>(h, s, 0.5 * s.d.dt, 1)));
+      }
       s.staggered = true;
     }
     LOSS_TRY(ensure_amp(h, s, s.step + n));
   }
   // launch shapes and descriptors
   std::vector<LineGeom> gx, gz;
-  LOSS_TRY(batch_geoms(h, 2, LOSS_KERNEL_ACOUSTIC_X, 3, 4, gx, &B.xlogc, &B.xthreads, &B.xsmem));
-  LOSS_TRY(batch_geoms(h, 0, LOSS_KERNEL_ACOUSTIC_Z, 2, 0, gz, &B.zlogc, &B.zthreads, &B.zsmem));
+  if (!B.conv) {
+    LOSS_TRY(batch_geoms(h, 2, LOSS_KERNEL_ACOUSTIC_X, 3, 4, gx, &B.xlogc, &B.xthreads, &B.xsmem));
+    LOSS_TRY(batch_geoms(h, 0, LOSS_KERNEL_ACOUSTIC_Z, 2, 0, gz, &B.zlogc, &B.zthreads, &B.zsmem));
+  }
   if (B.clk_cap < S) {
     if (B.clk) dev_free(h, B.clk);
     void* p = nullptr;
@@ -621,13 +778,15 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
   int64_t pre_max = 0, post_max = 0;
   for (int i = 0; i < S; ++i) {
     Shot& s = h->shots[i];
-    xa[i] = ac_x_args<T>(h, s, gx[i], 1, s.d.dt, 0.0);
-    xa[i].src.on = (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE)) ? 1 : 0;
-    xa[i].src.amp_tab = s.amp_tab;
-    xa[i].src.clk = B.clk + i;
-    za[i] = ac_z_args<T>(h, s, gz[i], s.d.dt, 1);
-    t0[i + 1] = t0[i] + gx[i].nbundles;
-    t0[S + 1 + i + 1] = t0[S + 1 + i] + gz[i].nbundles;
+    if (!B.conv) {
+      xa[i] = ac_x_args<T>(h, s, gx[i], 1, s.d.dt, 0.0);
+      xa[i].src.on = (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE)) ? 1 : 0;
+      xa[i].src.amp_tab = s.amp_tab;
+      xa[i].src.clk = B.clk + i;
+      za[i] = ac_z_args<T>(h, s, gz[i], s.d.dt, 1);
+      t0[i + 1] = t0[i] + gx[i].nbundles;
+      t0[S + 1 + i + 1] = t0[S + 1 + i] + gz[i].nbundles;
+    }
     for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {
       if (s.n_rcv == 0) break;
       const int64_t off = s.rcv_offsets[f], cnt = s.rcv_offsets[f + 1] - off;
@@ -662,11 +821,15 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
   B.post_max = post_max;
   std::vector<GatherJob<T>> jobs = pre;
   jobs.insert(jobs.end(), post.begin(), post.end());
-  LOSS_TRY(upload_table(h, 0, as_bytes(xa), &B.xtab));
-  LOSS_TRY(upload_table(h, 1, as_bytes(za), &B.ztab));
-  void* t0p = B.tile0;
-  LOSS_TRY(upload_table(h, 2, as_bytes(t0), &t0p));
-  B.tile0 = (int*)t0p;
+  if (B.conv) {
+    if constexpr (sizeof(T) == 4) LOSS_TRY(conv_tables<K>(h));
+  } else {
+    LOSS_TRY(upload_table(h, 0, as_bytes(xa), &B.xtab));
+    LOSS_TRY(upload_table(h, 1, as_bytes(za), &B.ztab));
+    void* t0p = B.tile0;
+    LOSS_TRY(upload_table(h, 2, as_bytes(t0), &t0p));
+    B.tile0 = (int*)t0p;
+  }
   LOSS_TRY(upload_table(h, 3, as_bytes(jobs), &B.jobs));
   // device clocks: set from the host counters unless they already hold them
   std::vector<StepClock> ck(S);
@@ -678,10 +841,12 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
                         "upload clocks"));
     LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
   }
-  LOSS_TRY(cuda_check(h, batch_grid_ac_x<T, K>(B.xlogc, B.xthreads, B.xsmem, B.xtiles, h->num_sms, &B.xgrid),
-                      "batched x kernel shape"));
-  LOSS_TRY(cuda_check(h, batch_grid_ac_z<T, K>(B.zlogc, B.zthreads, B.zsmem, B.ztiles, h->num_sms, &B.zgrid),
-                      "batched z kernel shape"));
+  if (!B.conv) {
+    LOSS_TRY(cuda_check(h, batch_grid_ac_x<T, K>(B.xlogc, B.xthreads, B.xsmem, B.xtiles, h->num_sms, &B.xgrid),
+                        "batched x kernel shape"));
+    LOSS_TRY(cuda_check(h, batch_grid_ac_z<T, K>(B.zlogc, B.zthreads, B.zsmem, B.ztiles, h->num_sms, &B.zgrid),
+                        "batched z kernel shape"));
+  }
   // launches
   int64_t done = 0;
   const int64_t k = h->graph_steps;
@@ -690,7 +855,10 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
                                       (int64_t)B.zsmem, B.zlogc, B.ztiles, B.zgrid, B.npre, B.npost, B.pre_max,
                                       B.post_max, (int64_t)(intptr_t)B.xtab, (int64_t)(intptr_t)B.ztab,
                                       (int64_t)(intptr_t)B.tile0, (int64_t)(intptr_t)B.jobs,
-                                      (int64_t)(intptr_t)B.clk, S, (int64_t)sizeof(T), K ? 1 : 0, k};
+                                      (int64_t)(intptr_t)B.clk, S, (int64_t)sizeof(T), K ? 1 : 0, k, B.conv ? 1 : 0,
+                                      (int64_t)(intptr_t)B.xptab, (int64_t)(intptr_t)B.tztab, B.xpgrid, B.xpthreads,
+                                      B.xl.total, B.tzthreads, B.tztiles, B.tzgrid[0], B.tzgrid[1],
+                                      (int64_t)B.tzsmem[0], (int64_t)B.tzsmem[1]};
     if (!B.gexec || sig != B.gsig) {
       LOSS_TRY((capture_graph<T, K>(h, k)));
       B.gsig = sig;

@@ -247,4 +247,31 @@ struct InjectJob {
   int64_t cnt;
 };
 
+// Dynamic shared memory of k_xp, in floats: 2 stages x NA staged rows of RW floats, the slow chunks' derivative
+// values O, the junction-correction weights (FP64), 2 stages x 2 layer segments (F floats each) of the x memory
+// variables, the warm-up partial sums PA / PB, and the x layer's coefficient tables (B step, A step, A half step;
+// 4 rows of F each).
+struct XpSmem {
+  int NA, RW, O, WS, SEG, F, PA, PB, TAB, DL, total;
+};
+// Descriptor of one shot in a batched z launch.
+struct TzShot {
+  AcZArgs<float> a;
+  TileGeom t;
+  int nwj;  // warps of the shot's single-shot launch
+  int pad;
+};
+
+// Descriptor of one shot in a batched x launch: its rows come in units of R consecutive rows, the global units
+// unit0 .. unit0 + ceil(t.ncross / R) - 1.
+constexpr int kXpMaxGroups = 8;
+struct XpShot {
+  AcXArgs<float> a;
+  TileGeom t;
+  unsigned mmagic;
+  int unit0;
+  int R;
+  int pad;
+};
+
 }  // namespace lossk

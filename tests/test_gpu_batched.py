@@ -1,8 +1,9 @@
 """GPU tests of the batched schedule (many 2-D acoustic shots of uneven size advanced by one persistent launch per
 kernel, optionally replayed from a captured CUDA graph) and of the autotuner, through the C ABI.
 
-The batched schedule performs the arithmetic of the per-shot schedule, so the two are compared for exact
-equality of every field and trace; the batched FP64 run is also compared with the FP64 oracle per shot."""
+The batched schedule performs the arithmetic of the per-shot schedule of the same kernel family (line kernels, or
+the FP32 truncated-convolution kernels), so the two are compared for exact equality of every field and trace; the
+batched FP64 run is also compared with the FP64 oracle per shot."""
 import dataclasses
 
 import numpy as np
@@ -38,9 +39,23 @@ def _shots(prec="fp64"):
     return out
 
 
-def _run(pkg, ws, batched, graph_steps, chunks):
+def _conv_shots(prec):
+    """Three shots whose patch lengths (32, 32, 16) are multiples of 8, so that both FP32 convolution kernels take
+    them; receivers as in _shots."""
+    ws = [acoustic2d_small(n=64, p=2, n_nb=12, steps=40, pml_width=10),
+          acoustic2d_small(n=96, p=3, n_nb=10, steps=40, pml_width=12),
+          acoustic2d_small(n=48, p=3, n_nb=8, steps=40, pml_width=8)]
+    out = []
+    for w in ws:
+        top = np.arange(w.n[1] + 1, dtype=np.int64)
+        out.append(dataclasses.replace(w, receivers={"sigma": top, "v1": top, "v3": top}, precision=prec,
+                                       f0=40.0, t0=1.2 / 40.0))
+    return out
+
+
+def _run(pkg, ws, batched, graph_steps, chunks, family="line"):
     g = pkg.Grid.from_workloads(ws)
-    g.set_kernels("line")  # the batched schedule runs the line kernels
+    g.set_kernels(family)
     g.set_schedule(batched, graph_steps)
     for c in chunks:
         g.step(c)
@@ -77,6 +92,28 @@ def test_graph_replay_equals_per_shot(pkg, prec):
     _assert_same(_run(pkg, ws, True, 7, [17, 23]), ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
+def test_batched_convolution_equals_per_shot(pkg, prec):
+    ws = _conv_shots(prec)
+    ref = _run(pkg, ws, False, 0, [17, 23], "convolution")
+    _assert_same(_run(pkg, ws, True, 0, [17, 23], "convolution"), ref)
+    _assert_same(_run(pkg, ws, True, 7, [17, 23], "convolution"), ref)
+
+
+def test_batched_convolution_against_oracle(pkg):
+    ws = _conv_shots("fp32_kahan")
+    g = pkg.Grid.from_workloads(ws)
+    g.set_schedule(True, 5)
+    g.step(40)
+    for s, w in enumerate(ws):
+        sim = Simulation(dataclasses.replace(w, precision="fp64")).step(40)
+        for f in ("sigma", "v1", "v3"):
+            ref = sim.state[f]
+            err = np.linalg.norm(g.get_field(s, f).astype(np.float64) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (s, f, err)
+    g.close()
+
+
 def test_graph_single_shot(pkg):
     ws = _shots("fp32")[:1]
     ref = _run(pkg, ws, False, 0, [12, 9])
@@ -102,14 +139,15 @@ def test_batched_fp64_against_oracle(pkg):
     g.close()
 
 
-def test_interleaved_reads_and_records(pkg):
+@pytest.mark.parametrize("family", ["line", "convolution"])
+def test_interleaved_reads_and_records(pkg, family):
     """Velocity reads (which bring a shot back to integer time), trace reads and a state round trip between
     graph-replayed batched runs give the same results as the same sequence on the per-shot schedule."""
-    ws = _shots("fp64")
+    ws = _shots("fp64") if family == "line" else _conv_shots("fp32_kahan")
 
     def seq(batched, graph_steps):
         g = pkg.Grid.from_workloads(ws)
-        g.set_kernels("line")
+        g.set_kernels(family)
         g.set_schedule(batched, graph_steps)
         g.step(10)
         v = g.get_field(1, "v1")
@@ -149,16 +187,18 @@ def test_autotune(pkg):
     g.close()
 
 
-def test_full_survey_batched(pkg):
+@pytest.mark.parametrize("family", ["convolution", "line"])
+def test_full_survey_batched(pkg, family):
     """The 64-shot survey (n from 512 to 2048, M = 128, n_nb = 20, 40-point layers, FP32): three graph-replayed
-    steps equal the per-shot schedule exactly on every shot, and the smallest and largest shots match the FP64
-    oracle after the same steps."""
+    steps equal the per-shot schedule of the same kernel family exactly on every shot, and the smallest and
+    largest shots match the FP64 oracle after the same steps."""
     ws = batched_shots(steps=3)
     g = pkg.Grid.from_workloads(ws)
+    g.set_kernels(family)
     g.set_schedule(True, 3)
     g.step(3)
     r = pkg.Grid.from_workloads(ws)
-    r.set_kernels("line")
+    r.set_kernels(family)
     r.set_schedule(False, 0)
     r.step(3)
     for s in range(len(ws)):
