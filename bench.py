@@ -205,12 +205,16 @@ def _batched_leg(torch, pkg, units, warmup_units, k):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / (units * k)
     launches = g.profile_read(-1)[1]
+    conv = g.profile_read("acoustic_z2")[1] > 0  # the convolution kernels split z into Z1 and Z2
     g.close()
     peak, kind = _peaks()
-    alg = 40  # B per point-step: x kernel 24 (v1, sigma, kappa, d_z v3 read; sigma, v1 written), z kernel 16
+    # B per point-step: x kernel 24 (v1, sigma, kappa, d_z v3 read; sigma, v1 written); z: line kernel 16 (sigma, v3
+    # read; v3, d_z v3 written), or Z1 12 (sigma, v3 read; v3 written) + Z2 8 (v3 read; d_z v3 written)
+    alg = 44 if conv else 40
     value = pts / (ms * 1e-3)
     return {"workload": f"{len(ws)} shots, n from {min(w.n[0] for w in ws)} to {max(w.n[0] for w in ws)}, M=128, "
                         f"n_nb=20, PML 40, FP32, graph of {k} steps",
+            "kernels": "truncated-convolution" if conv else "line",
             "points_per_step": pts, "value": value, "unit": UNIT, "ms_per_step": ms,
             "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9), "peak_kind": peak_kind_note(kind),
             "autotune": tune, "launches": launches, "l2": "working set 4.5 GB, no flush"}

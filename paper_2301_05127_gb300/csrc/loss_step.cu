@@ -635,6 +635,7 @@ static bool conv_batch_ok(const loss_ctx* h) {
     ts.push_back(t);
     threads = std::max(threads, thr);
   }
+  while (threads & (threads - 1)) threads += 32;
   std::vector<int> rs;
   for (const TileGeom& t : ts) rs.push_back(xp_rows_per_unit(t.n, threads));
   return !ts.empty() &&
@@ -659,6 +660,7 @@ static loss_status_t conv_tables(loss_ctx* h) {
     tile_geom(h->shots[i], 2, &thr);
     xthreads = std::max(xthreads, thr);
   }
+  while (xthreads & (xthreads - 1)) xthreads += 32;  // a power of two of warps, so that short rows form groups
   for (int i = 0; i < S; ++i) {
     Shot& s = h->shots[i];
     LOSS_TRY(ensure_delta_weights(h, s, 0));
