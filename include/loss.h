@@ -229,7 +229,10 @@ loss_status_t loss_set_launch(loss_handle_t handle, int32_t kernel, int32_t line
  * is the thread count a block of this kernel aims at; every shot then takes the widest power-of-two bundle of
  * whole lines whose chunks fit in it (so shots of different sizes share one block size in a batched launch).
  * chunk_log2 as in loss_set_launch.  0 = the built-in choice.  An explicit lines_per_block (loss_set_launch)
- * takes precedence.  Used by the autotuner.  LOSS_E_ARG for values out of range. */
+ * takes precedence.  For the truncated-convolution z tiles (LOSS_KERNEL_ACOUSTIC_Z = Z1, LOSS_KERNEL_ACOUSTIC_Z2 =
+ * Z2) chunk_log2 is the number of z positions one warp row of a tile takes (8 or 16; 0 = 16) and fixes the block
+ * size, 32 x ceil(M / chunk); threads_per_block does not apply to them.  Used by the autotuner.  LOSS_E_ARG for
+ * values out of range. */
 loss_status_t loss_set_tile(loss_handle_t handle, int32_t kernel, int32_t threads_per_block, int32_t chunk_log2);
 
 /* Schedule of loss_step (spec batching pattern; the paper's MPI design runs one process per patch instead).
@@ -263,8 +266,9 @@ typedef struct {
 } loss_tune_entry_t;
 
 /* Project-written autotuner (spec batching pattern): times every candidate tile shape (threads per block
- * 128..1024, chunk_log2 3 or 4) of each kernel family the handle's time step uses, on a scratch copy of the
- * handle (same grids, models, absorbing layers and schedule; zero fields), with `steps` timed steps per candidate
+ * 128..1024, chunk_log2 3 or 4; for the convolution kernels the z chunk of Z1 and Z2) of each kernel family the
+ * handle's time step uses, on a scratch copy of the handle (same grids, models, absorbing layers, kernel family
+ * and schedule; zero fields), with `steps` timed steps per candidate
  * after one warm-up step, and applies the fastest shape of each family to the handle (loss_set_tile).  The
  * handle's own state is not touched.  out (capacity cap entries, may be NULL) receives one entry per tuned
  * family and *n_out their number.  Needs device memory for a second copy of the handle's arrays.

@@ -581,6 +581,7 @@ loss_status_t loss_autotune(loss_handle_t h, int32_t steps, loss_tune_entry_t* o
   }
   std::vector<int> kids;
   if (ac) kids.insert(kids.end(), {LOSS_KERNEL_ACOUSTIC_X, LOSS_KERNEL_ACOUSTIC_Z});
+  if (ac && conv_z_used(h)) kids.push_back(LOSS_KERNEL_ACOUSTIC_Z2);  // the convolution z tiles: Z1 and Z2
   if (el) kids.insert(kids.end(), {LOSS_KERNEL_ELASTIC_X, LOSS_KERNEL_ELASTIC_Y, LOSS_KERNEL_ELASTIC_Z});
   // candidates: (threads, chunk_log2)
   std::vector<std::pair<int, int>> cand;
@@ -629,6 +630,7 @@ loss_status_t loss_autotune(loss_handle_t h, int32_t steps, loss_tune_entry_t* o
     for (int k = 0; k < 25; ++k) b.src_g[k] = a.src_g[k];
   }
   t->batched = h->batched;
+  t->tiled = h->tiled;
   t->graph_steps = 0;  // plain launches, so that every kernel can be timed
   for (int k = 0; k < LOSS_NUM_KERNELS; ++k) {
     t->tile_threads[k] = h->tile_threads[k];

@@ -107,8 +107,8 @@ struct BatchState {
   void* xptab = nullptr;  // XpShot[n_shots]
   void* tztab = nullptr;  // TzShot[2 n_shots]
   XpSmem xl{};
-  int xpthreads = 0, xpgrid = 0, tzthreads = 0, tztiles = 0;
-  int tzgrid[2] = {0, 0};
+  int xpthreads = 0, xpgrid = 0, tztiles = 0;
+  int tzthreads[2] = {0, 0}, tzlogc[2] = {4, 4}, tzgrid[2] = {0, 0};
   size_t tzsmem[2] = {0, 0};
 };
 
@@ -192,6 +192,7 @@ loss_status_t step_shot(loss_ctx* h, Shot& s);
 loss_status_t unstagger(loss_ctx* h, Shot& s);
 loss_status_t stagger_shot(loss_ctx* h, Shot& s);
 bool batch_eligible(const loss_ctx* h);
+bool conv_z_used(const loss_ctx* h);  // some shot's FP32 step runs the convolution z tiles
 loss_status_t step_batched(loss_ctx* h, int64_t n_steps);
 void batch_release(loss_ctx* h);
 void batch_destroy(loss_ctx* h);
@@ -223,7 +224,7 @@ template <typename T>
 cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
 cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
 template <bool KAHAN>
-cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int threads, cudaStream_t st);
+cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int threads, int logc, cudaStream_t st);
 template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
                       cudaStream_t st);
@@ -238,9 +239,9 @@ template <bool KAHAN>
 cudaError_t xp_batch_per_sm(const XpSmem& L, int threads, int* per_sm);
 template <bool KAHAN>
 cudaError_t launch_tz_batch(const TzShot* tab, const int* tile0, int nshots, int ntiles, int mode, int threads,
-                            size_t smem, int grid, cudaStream_t st);
+                            int logc, size_t smem, int grid, cudaStream_t st);
 template <bool KAHAN>
-cudaError_t tz_batch_per_sm(int mode, int threads, size_t smem, int* per_sm);
+cudaError_t tz_batch_per_sm(int mode, int threads, int logc, size_t smem, int* per_sm);
 template <typename T>
 cudaError_t launch_adj(const AdjArgs<T>& a, int logc, bool sflav, int threads, cudaStream_t st);
 template <typename T>

@@ -199,7 +199,7 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
   }
 }
 
-// One shot: one block per tile, 32 x ceil(M / 16) threads.
+// One shot: one block per tile, 32 x ceil(M / C) threads.
 template <int MODE, bool KAHAN, int LOGC>
 __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -948,13 +948,18 @@ static cudaError_t tile_launch(K kern, int grid, int threads, size_t smem, cudaS
   return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(threads), argv, smem, st);
 }
 
+// logc: log2 of the z positions one warp row takes (3 or 4).
 template <bool KAHAN>
-cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int threads, cudaStream_t st) {
+cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int threads, int logc, cudaStream_t st) {
   AcZArgs<float> aa = a;
   TileGeom tt = t;
   void* argv[] = {&aa, &tt};
   const int grid = t.ntl * t.p;
   const size_t smem = tile_smem_z(t, mode);
+  if (logc == 3) {
+    if (mode == 1) return tile_launch(k_tz<1, KAHAN, 3>, grid, threads, smem, st, argv);
+    return tile_launch(k_tz<2, KAHAN, 3>, grid, threads, smem, st, argv);
+  }
   if (mode == 1) return tile_launch(k_tz<1, KAHAN, 4>, grid, threads, smem, st, argv);
   return tile_launch(k_tz<2, KAHAN, 4>, grid, threads, smem, st, argv);
 }
@@ -1013,17 +1018,21 @@ cudaError_t xp_batch_per_sm(const XpSmem& L, int threads, int* per_sm) {
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_xp_batch<KAHAN>, threads, (size_t)L.total * 4);
 }
-template <bool KAHAN>
-cudaError_t launch_tz_batch(const TzShot* tab, const int* tile0, int nshots, int ntiles, int mode, int threads,
-                            size_t smem, int grid, cudaStream_t st) {
-  if (grid <= 0 || ntiles <= 0) return cudaSuccess;
-  void* argv[] = {(void*)&tab, (void*)&tile0, (void*)&nshots, (void*)&ntiles};
-  if (mode == 1) return tile_launch(k_tz_batch<1, KAHAN, 4>, grid, threads, smem, st, argv);
-  return tile_launch(k_tz_batch<2, KAHAN, 4>, grid, threads, smem, st, argv);
+template <int MODE, bool KAHAN>
+static auto tz_batch_kernel(int logc) {
+  return logc == 3 ? k_tz_batch<MODE, KAHAN, 3> : k_tz_batch<MODE, KAHAN, 4>;
 }
 template <bool KAHAN>
-cudaError_t tz_batch_per_sm(int mode, int threads, size_t smem, int* per_sm) {
-  auto kern = mode == 1 ? k_tz_batch<1, KAHAN, 4> : k_tz_batch<2, KAHAN, 4>;
+cudaError_t launch_tz_batch(const TzShot* tab, const int* tile0, int nshots, int ntiles, int mode, int threads,
+                            int logc, size_t smem, int grid, cudaStream_t st) {
+  if (grid <= 0 || ntiles <= 0) return cudaSuccess;
+  void* argv[] = {(void*)&tab, (void*)&tile0, (void*)&nshots, (void*)&ntiles};
+  if (mode == 1) return tile_launch(tz_batch_kernel<1, KAHAN>(logc), grid, threads, smem, st, argv);
+  return tile_launch(tz_batch_kernel<2, KAHAN>(logc), grid, threads, smem, st, argv);
+}
+template <bool KAHAN>
+cudaError_t tz_batch_per_sm(int mode, int threads, int logc, size_t smem, int* per_sm) {
+  auto kern = mode == 1 ? tz_batch_kernel<1, KAHAN>(logc) : tz_batch_kernel<2, KAHAN>(logc);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
@@ -1034,10 +1043,12 @@ template cudaError_t launch_xp_batch<true>(const XpShot*, const int*, const int*
                                            int*, cudaStream_t);
 template cudaError_t xp_batch_per_sm<false>(const XpSmem&, int, int*);
 template cudaError_t xp_batch_per_sm<true>(const XpSmem&, int, int*);
-template cudaError_t launch_tz_batch<false>(const TzShot*, const int*, int, int, int, int, size_t, int, cudaStream_t);
-template cudaError_t launch_tz_batch<true>(const TzShot*, const int*, int, int, int, int, size_t, int, cudaStream_t);
-template cudaError_t tz_batch_per_sm<false>(int, int, size_t, int*);
-template cudaError_t tz_batch_per_sm<true>(int, int, size_t, int*);
+template cudaError_t launch_tz_batch<false>(const TzShot*, const int*, int, int, int, int, int, size_t, int,
+                                            cudaStream_t);
+template cudaError_t launch_tz_batch<true>(const TzShot*, const int*, int, int, int, int, int, size_t, int,
+                                           cudaStream_t);
+template cudaError_t tz_batch_per_sm<false>(int, int, int, size_t, int*);
+template cudaError_t tz_batch_per_sm<true>(int, int, int, size_t, int*);
 
 template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
@@ -1054,7 +1065,7 @@ cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagi
 template cudaError_t launch_xp<false>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);
 template cudaError_t launch_xp<true>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);
 
-template cudaError_t launch_tz<false>(const AcZArgs<float>&, const TileGeom&, int, int, cudaStream_t);
-template cudaError_t launch_tz<true>(const AcZArgs<float>&, const TileGeom&, int, int, cudaStream_t);
+template cudaError_t launch_tz<false>(const AcZArgs<float>&, const TileGeom&, int, int, int, cudaStream_t);
+template cudaError_t launch_tz<true>(const AcZArgs<float>&, const TileGeom&, int, int, int, cudaStream_t);
 
 }  // namespace lossk

@@ -143,8 +143,8 @@ static bool tiled_ok(const loss_ctx* h, const Shot& s) {
   return Mz <= 512 && std::max(s.d.n_nb, FirLen<float>::K) <= 64;
 }
 
-// z tiles: 32 columns x one patch, C = 16 positions per thread; x tiles: R rows x one patch, C = 8.
-static TileGeom tile_geom(const Shot& s, int k, int* threads) {
+// z tiles: 32 columns x one patch, C = 2^zlogc positions per thread (a warp row); x rows: C = 8.
+static TileGeom tile_geom(const Shot& s, int k, int* threads, int zlogc = 4) {
   TileGeom t{};
   t.n = (int)s.n[k];
   t.p = s.p[k];
@@ -166,7 +166,8 @@ static TileGeom tile_geom(const Shot& s, int k, int* threads) {
     t.ncross = (int)s.len[2];
     t.ntl = (t.ncross + 31) / 32;
     t.R = 32;
-    *threads = 32 * ((t.M + 15) / 16);
+    const int C = 1 << zlogc;
+    *threads = 32 * ((t.M + C - 1) / C);
   } else {
     t.ncross = (int)s.len[0];
     t.ntl = t.ncross;
@@ -214,14 +215,27 @@ static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double 
   return ac_x<float, K>(h, s, do_B, acoef, amp);
 }
 
+bool conv_z_used(const loss_ctx* h) {
+  for (const Shot& s : h->shots)
+    if (tiled_ok(h, s)) return true;
+  return false;
+}
+
+// log2 of the z tile chunk of Z1 (mode 1) or Z2 (mode 2): the tuned value, else 16 positions.
+static int zchunk_log2(const loss_ctx* h, int mode) {
+  const int c = h->chunk_log2[mode == 1 ? LOSS_KERNEL_ACOUSTIC_Z : LOSS_KERNEL_ACOUSTIC_Z2];
+  return c == 3 ? 3 : 4;
+}
+
 template <bool K>
 static loss_status_t tz(loss_ctx* h, Shot& s, int mode, double acoef) {
   LOSS_TRY(ensure_delta_weights(h, s, 0));
   int threads;
-  const TileGeom t = tile_geom(s, 0, &threads);
+  const int lc = zchunk_log2(h, mode);
+  const TileGeom t = tile_geom(s, 0, &threads, lc);
   const AcZArgs<float> a = ac_z_args<float>(h, s, LineGeom{}, acoef, 0);
   LaunchScope ls(h, mode == 1 ? LOSS_KERNEL_ACOUSTIC_Z : LOSS_KERNEL_ACOUSTIC_Z2);
-  return cuda_check(h, launch_tz<K>(a, t, mode, threads, h->stream), "acoustic z tile kernel");
+  return cuda_check(h, launch_tz<K>(a, t, mode, threads, lc, h->stream), "acoustic z tile kernel");
 }
 
 template <typename T>
@@ -550,7 +564,8 @@ static loss_status_t batch_launch_step(loss_ctx* h) {
       for (int mode = 1; mode <= 2; ++mode) {
         LaunchScope ls(h, mode == 1 ? LOSS_KERNEL_ACOUSTIC_Z : LOSS_KERNEL_ACOUSTIC_Z2);
         LOSS_TRY(cuda_check(h, launch_tz_batch<K>((const TzShot*)B.tztab + (mode - 1) * S, zt0, S, B.tztiles, mode,
-                                                  B.tzthreads, B.tzsmem[mode - 1], B.tzgrid[mode - 1], h->stream),
+                                                  B.tzthreads[mode - 1], B.tzlogc[mode - 1], B.tzsmem[mode - 1],
+                                                  B.tzgrid[mode - 1], h->stream),
                             "batched acoustic z tile kernel"));
       }
       if (B.npost) {
@@ -622,13 +637,18 @@ static loss_status_t capture_graph(loss_ctx* h, int64_t k) {
   return LOSS_OK;
 }
 
-// Every shot takes the FP32 truncated-convolution kernels (z tiles of patches of at most 256 points and the
-// pipelined x kernel), and their batched x layout fits shared memory.
+// Every shot takes the FP32 truncated-convolution kernels (z tiles of at most 512 threads and the pipelined x
+// kernel), and their batched x layout fits shared memory.
 static bool conv_batch_ok(const loss_ctx* h) {
   std::vector<TileGeom> ts;
   int threads = 32;
   for (const Shot& s : h->shots) {
-    if (!tiled_ok(h, s) || s.n[0] / s.p[0] > 256) return false;
+    if (!tiled_ok(h, s)) return false;
+    for (int mode = 1; mode <= 2; ++mode) {  // batched z blocks hold at most 512 threads
+      int zt;
+      tile_geom(s, 0, &zt, zchunk_log2(h, mode));
+      if (zt > 512) return false;
+    }
     int thr;
     TileGeom t = tile_geom(s, 2, &thr);
     if (!xp_ok(h, s, t)) return false;
@@ -652,7 +672,8 @@ static loss_status_t conv_tables(loss_ctx* h) {
   std::vector<TzShot> zs(2 * S);
   std::vector<TileGeom> txs(S);
   std::vector<int> unit0(S + 1, 0), zt0(S + 1, 0), rs(S);
-  int xthreads = 32, zthreads = 32;
+  int xthreads = 32, zthreads[2] = {32, 32};
+  const int zlc[2] = {zchunk_log2(h, 1), zchunk_log2(h, 2)};
   size_t zsm[2] = {0, 0};
   int64_t ptot = 0;
   for (int i = 0; i < S; ++i) {
@@ -682,13 +703,13 @@ static loss_status_t conv_tables(loss_ctx* h) {
     unit0[i + 1] = unit0[i] + (tx.ncross + rs[i] - 1) / rs[i];
     ptot += (int64_t)(tx.n + 1) * tx.ncross;
     txs[i] = tx;
-    const TileGeom tz = tile_geom(s, 0, &thr);
-    zs[i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, s.d.dt, 0), tz, thr >> 5, 0};
-    zs[S + i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, 0.0, 0), tz, thr >> 5, 0};
-    zthreads = std::max(zthreads, thr);
-    zsm[0] = std::max(zsm[0], tile_smem_z(tz, 1));
-    zsm[1] = std::max(zsm[1], tile_smem_z(tz, 2));
-    zt0[i + 1] = zt0[i] + tz.ntl * tz.p;
+    for (int m = 0; m < 2; ++m) {
+      const TileGeom tz = tile_geom(s, 0, &thr, zlc[m]);
+      zs[m * S + i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, m == 0 ? s.d.dt : 0.0, 0), tz, thr >> 5, 0};
+      zthreads[m] = std::max(zthreads[m], thr);
+      zsm[m] = std::max(zsm[m], tile_smem_z(tz, m + 1));
+      if (m == 0) zt0[i + 1] = zt0[i] + tz.ntl * tz.p;
+    }
   }
   B.xl = xp_batch_layout(txs, rs, K);
   B.xpthreads = xthreads;
@@ -715,11 +736,12 @@ static loss_status_t conv_tables(loss_ctx* h) {
       }
   }
   B.xpgrid = G;
-  B.tzthreads = zthreads;
   B.tztiles = zt0[S];
   for (int m = 0; m < 2; ++m) {
     B.tzsmem[m] = zsm[m];
-    LOSS_TRY(cuda_check(h, tz_batch_per_sm<K>(m + 1, zthreads, zsm[m], &per), "batched z kernel shape"));
+    B.tzthreads[m] = zthreads[m];
+    B.tzlogc[m] = zlc[m];
+    LOSS_TRY(cuda_check(h, tz_batch_per_sm<K>(m + 1, zthreads[m], zlc[m], zsm[m], &per), "batched z kernel shape"));
     if (per < 1) {
       h->err = "batched z kernel does not fit an SM";
       return LOSS_E_UNSUPPORTED;
@@ -859,7 +881,8 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
                                       (int64_t)(intptr_t)B.tile0, (int64_t)(intptr_t)B.jobs,
                                       (int64_t)(intptr_t)B.clk, S, (int64_t)sizeof(T), K ? 1 : 0, k, B.conv ? 1 : 0,
                                       (int64_t)(intptr_t)B.xptab, (int64_t)(intptr_t)B.tztab, B.xpgrid, B.xpthreads,
-                                      B.xl.total, B.tzthreads, B.tztiles, B.tzgrid[0], B.tzgrid[1],
+                                      B.xl.total, B.tzthreads[0], B.tzthreads[1], B.tzlogc[0], B.tzlogc[1],
+                                      B.tztiles, B.tzgrid[0], B.tzgrid[1],
                                       (int64_t)B.tzsmem[0], (int64_t)B.tzsmem[1]};
     if (!B.gexec || sig != B.gsig) {
       LOSS_TRY((capture_graph<T, K>(h, k)));

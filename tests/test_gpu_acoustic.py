@@ -35,7 +35,10 @@ def rel(a, b):
 def _compare(pkg, w, prec, steps, every=50, family=None):
     g = pkg.Grid.from_workloads([w], precision=prec)
     if family:
-        g.set_kernels(family)
+        g.set_kernels(family.split("/")[0])
+        if family.endswith("/z8"):  # convolution z tiles with 8 positions per warp row
+            g.set_tile("acoustic_z", 0, 3)
+            g.set_tile("acoustic_z2", 0, 3)
     sim = Simulation(w)
     fields = ("sigma", "v1", "v3")
     peak = {f: 0.0 for f in fields}
@@ -162,7 +165,7 @@ def test_velocity_receivers_inside_the_layer(pkg):
     g.close()
 
 
-@pytest.mark.parametrize("family", ["line", "convolution"])
+@pytest.mark.parametrize("family", ["line", "convolution", "convolution/z8"])
 @pytest.mark.parametrize("geom", [
     # (n_z, n_x, p_z, p_x, n_nb, layer): patch lengths shorter than the convolution's truncation length (16),
     # not multiples of 8 (x falls back to the line kernel), a single-warp z tile, x extents that are not multiples

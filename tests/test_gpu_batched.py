@@ -53,9 +53,12 @@ def _conv_shots(prec):
     return out
 
 
-def _run(pkg, ws, batched, graph_steps, chunks, family="line"):
+def _run(pkg, ws, batched, graph_steps, chunks, family="line", zchunk_log2=0):
     g = pkg.Grid.from_workloads(ws)
     g.set_kernels(family)
+    if zchunk_log2:  # z positions per warp row of the convolution z tiles (Z1 and Z2)
+        g.set_tile("acoustic_z", 0, zchunk_log2)
+        g.set_tile("acoustic_z2", 0, zchunk_log2)
     g.set_schedule(batched, graph_steps)
     for c in chunks:
         g.step(c)
@@ -92,12 +95,13 @@ def test_graph_replay_equals_per_shot(pkg, prec):
     _assert_same(_run(pkg, ws, True, 7, [17, 23]), ref)
 
 
+@pytest.mark.parametrize("zchunk_log2", [4, 3])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
-def test_batched_convolution_equals_per_shot(pkg, prec):
+def test_batched_convolution_equals_per_shot(pkg, prec, zchunk_log2):
     ws = _conv_shots(prec)
-    ref = _run(pkg, ws, False, 0, [17, 23], "convolution")
-    _assert_same(_run(pkg, ws, True, 0, [17, 23], "convolution"), ref)
-    _assert_same(_run(pkg, ws, True, 7, [17, 23], "convolution"), ref)
+    ref = _run(pkg, ws, False, 0, [17, 23], "convolution", zchunk_log2)
+    _assert_same(_run(pkg, ws, True, 0, [17, 23], "convolution", zchunk_log2), ref)
+    _assert_same(_run(pkg, ws, True, 7, [17, 23], "convolution", zchunk_log2), ref)
 
 
 def test_batched_convolution_against_oracle(pkg):
@@ -175,7 +179,7 @@ def test_autotune(pkg):
     ws = _shots("fp32_kahan")
     g = pkg.Grid.from_workloads(ws)
     res = g.autotune(steps=2)
-    assert set(res) == {"acoustic_x", "acoustic_z"}
+    assert set(res) == {"acoustic_x", "acoustic_z"}  # a patch length of 12 keeps these shots on the line kernels
     for r in res.values():
         assert r["threads_per_block"] in (128, 256, 512, 1024) and r["chunk_log2"] in (3, 4) and r["ms"] > 0
     assert g.get_step(0) == 0 and not g.get_field(0, "sigma").any()
@@ -185,6 +189,28 @@ def test_autotune(pkg):
         ref = sim.state["sigma"]
         assert np.linalg.norm(g.get_field(s, "sigma") - ref) / np.linalg.norm(ref) < 1e-5
     g.close()
+
+
+def test_autotune_convolution(pkg):
+    """Shots that take the convolution kernels: the z chunk of Z1 and Z2 is tuned too, and the tuned handle still
+    equals the per-shot schedule with the same shapes."""
+    ws = _conv_shots("fp32_kahan")
+    g = pkg.Grid.from_workloads(ws)
+    res = g.autotune(steps=2)
+    assert set(res) == {"acoustic_x", "acoustic_z", "acoustic_z2"}
+    for k in ("acoustic_z", "acoustic_z2"):
+        assert res[k]["chunk_log2"] in (3, 4) and res[k]["ms"] > 0
+    g.step(17)
+    r = pkg.Grid.from_workloads(ws)
+    r.set_schedule(False, 0)
+    for k in ("acoustic_z", "acoustic_z2"):
+        r.set_tile(k, 0, res[k]["chunk_log2"])
+    r.step(17)
+    for s in range(len(ws)):
+        for f in ("sigma", "v1", "v3"):
+            assert np.array_equal(g.get_field(s, f), r.get_field(s, f)), (s, f)
+    g.close()
+    r.close()
 
 
 @pytest.mark.parametrize("family", ["convolution", "line"])
