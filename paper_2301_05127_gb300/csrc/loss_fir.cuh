@@ -59,110 +59,11 @@ __device__ __forceinline__ T fir_right(const T* __restrict__ f, const BUN& bun, 
   return s;
 }
 
-// FP32 -> FP64 widening on the integer units (IEEE 754: binary32 exponent bias 127, binary64 bias 1023, the 23
-// fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0.
-// Keeps the FP64 pipe, which is narrow on this GPU, free for the FMAs of the junction sums.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  return ex ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
-}
-
 // Truncation length: |r|^K below the working precision's rounding (7e-10 for FP32, 1e-16 for FP64).
 template <typename T>
 struct FirLen {
   static constexpr int K = sizeof(T) == 4 ? 16 : 28;
 };
-
-// PMBC closures phi_j (FP64 sums, as pmbc_phi) turned into the junction corrections D_j = phi_j - eF_j; also
-// fills the r^d table.  One group of G lanes per (line, junction).  Must be followed by __syncthreads().
-template <typename T, int G, class BUN>
-__device__ void fir_junctions(const T* __restrict__ f, const BUN& bun, int L, int nvalid, int n, int p, int M,
-                              int n_nb, const double* __restrict__ W, T r, T a, double* __restrict__ dl,
-                              T* __restrict__ rpow) {
-  constexpr int K = FirLen<T>::K;
-  if (threadIdx.x == 0) {
-    T q = T(1);
-    for (int d = 0; d < kFirPow; ++d) {
-      rpow[d] = q;
-      q *= r;
-    }
-  }
-  const int items = L * (p + 1);
-  const int g = threadIdx.x % G;
-  const int lane = threadIdx.x & 31;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const int wlen = 2 * n_nb + 1;
-  for (int it = threadIdx.x / G; it < items; it += blockDim.x / G) {
-    const int line = it / (p + 1);
-    const int j = it - line * (p + 1);
-    const int c = j * M;
-    const int mlo = max(-n_nb, -c);
-    const int mhi = min(n_nb, n - c);
-    double s = 0.0, s2 = 0.0;
-    if (line < nvalid) {
-      const double* wj = W + (size_t)j * wlen + n_nb;
-      int m = mlo + g;
-      for (; m + G <= mhi; m += 2 * G) {
-        s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
-        s2 = fma(__ldg(wj + m + G), (double)f[bun.at(line, c + m + G)], s2);
-      }
-      if (m <= mhi) s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
-      s += s2;
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
-    if (g == 0 && line < nvalid) {
-      const T eF = a * (fir_right<T, K>(f, bun, line, c, n, r) - fir_left<T, K>(f, bun, line, c, n, r));
-      dl[it] = s - (double)eF;
-    }
-  }
-}
-
-// e on the chunk [p0, p0 + len) of line l (len <= C): the particular solution plus the patch corrections.
-// dl: this line's D_j (p + 1 values); rho = r^M, inv = 1 / (1 - rho^2).
-template <typename T, int C, class BUN>
-__device__ __forceinline__ void fir_chunk(const T* __restrict__ f, const BUN& bun, int l, int p0, int len, int n,
-                                          int M, unsigned mmagic, T r, T a, T rho, T inv,
-                                          const double* __restrict__ dl, const T* __restrict__ rpow, T (&e)[C]) {
-  constexpr int K = FirLen<T>::K;
-  T fv[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j)
-    if (j < len) fv[j] = f[bun.at(l, p0 + j)];
-  T s = fir_left<T, K>(f, bun, l, p0, n, r);
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    if (j < len) {
-      e[j] = s;  // L_{p0+j}
-      s = fv[j] + r * s;
-    }
-  }
-  T q = fir_right<T, K>(f, bun, l, p0 + len - 1, n, r);
-#pragma unroll
-  for (int j = C - 1; j >= 0; --j) {
-    if (j < len) {
-      e[j] = a * (q - e[j]);
-      q = fv[j] + r * q;
-    }
-  }
-  // patch corrections (patches are at least 1 point long; r^d vanishes beyond the table)
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    if (j < len) {
-      const int pos = p0 + j;
-      const int pt = min((int)div_magic(pos, mmagic), (n - 1) / M);  // patch of pos (the last point: last patch)
-      const int d1 = pos - pt * M, d2 = M - d1;
-      if (d1 < kFirPow || d2 < kFirPow) {
-        const T DL = (T)dl[pt], DR = (T)dl[pt + 1];
-        const T A = (DL - rho * DR) * inv, B = (DR - rho * DL) * inv;
-        if (d1 < kFirPow) e[j] += A * rpow[d1];
-        if (d2 < kFirPow) e[j] += B * rpow[d2];
-      }
-    }
-  }
-}
 
 // Contiguous run of up to C + 1 floats starting at a 16-byte aligned address (16-byte accesses where possible).
 template <int C>

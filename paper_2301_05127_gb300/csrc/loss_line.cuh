@@ -84,6 +84,19 @@ struct Tab<double> {
   static __device__ __forceinline__ double m(const float*, const double* t64, int j) { return __ldg(t64 + j); }
 };
 
+// FP32 -> FP64 widening on the integer units (IEEE 754: binary32 exponent bias 127, binary64 bias 1023, the 23
+// fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0.
+// Keeps the FP64 pipe, which is narrow on this GPU, free for the FMAs of the junction sums.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return ex ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
+}
+
+__device__ __forceinline__ double to_f64(float f) { return widen(f); }
+__device__ __forceinline__ double to_f64(double f) { return f; }
+
 // PMBC sums phi[line][j] for all lines and junctions of a bundle, accumulated in double.  G threads share
 // one (line, junction) and combine partial sums with shuffles.  W is [(p+1)][2 n_nb + 1], already scaled.
 template <typename T, int G, class BUN>
@@ -105,10 +118,10 @@ __device__ void pmbc_phi(const T* __restrict__ f, const BUN& bun, int L, int nva
       const double* wj = W + (size_t)j * wlen + n_nb;
       int m = mlo + g;
       for (; m + G <= mhi; m += 2 * G) {
-        s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
-        s2 = fma(__ldg(wj + m + G), (double)f[bun.at(line, c + m + G)], s2);
+        s = fma(__ldg(wj + m), to_f64(f[bun.at(line, c + m)]), s);
+        s2 = fma(__ldg(wj + m + G), to_f64(f[bun.at(line, c + m + G)]), s2);
       }
-      if (m <= mhi) s = fma(__ldg(wj + m), (double)f[bun.at(line, c + m)], s);
+      if (m <= mhi) s = fma(__ldg(wj + m), to_f64(f[bun.at(line, c + m)]), s);
       s += s2;
     }
 #pragma unroll
