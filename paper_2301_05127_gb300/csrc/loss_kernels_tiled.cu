@@ -58,9 +58,16 @@ __device__ void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, i
     const int mlo = max(-t.Rd, -c);
     const int mhi = min(t.Rd, t.n - c);
     const double* wj = wsm + J * wl + t.Rd;
-    double s = 0.0;
-    if (col < nvalid)
-      for (int m = mlo + sub; m <= mhi; m += ns) s = fma(wj[m], widen(F[bun.at(col, c + m)]), s);
+    double s = 0.0, s2 = 0.0;  // two independent accumulators halve the FP64 dependency chain
+    if (col < nvalid) {
+      int m = mlo + sub;
+      for (; m + ns <= mhi; m += 2 * ns) {
+        s = fma(wj[m], widen(F[bun.at(col, c + m)]), s);
+        s2 = fma(wj[m + ns], widen(F[bun.at(col, c + m + ns)]), s2);
+      }
+      if (m <= mhi) s = fma(wj[m], widen(F[bun.at(col, c + m)]), s);
+      s += s2;
+    }
     partf[(J * ns + sub) * 32 + col] = s;
   }
   __syncthreads();
@@ -358,8 +365,14 @@ __device__ void xf_junctions(const float* __restrict__ row, const BUN& bun, cons
     const int mlo = max(-t.Rd, -c);
     const int mhi = min(t.Rd, t.n - c);
     const double* wj = wd + (size_t)j * wl + t.Rd;
-    double s = 0.0;
-    for (int m = mlo + g; m <= mhi; m += G) s = fma(wj[m], widen(row[bun.at(0, c + m)]), s);
+    double s = 0.0, s2 = 0.0;  // two independent accumulators halve the FP64 dependency chain
+    int m = mlo + g;
+    for (; m + G <= mhi; m += 2 * G) {
+      s = fma(wj[m], widen(row[bun.at(0, c + m)]), s);
+      s2 = fma(wj[m + G], widen(row[bun.at(0, c + m + G)]), s2);
+    }
+    if (m <= mhi) s = fma(wj[m], widen(row[bun.at(0, c + m)]), s);
+    s += s2;
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
     if (g == 0) dlf[j] = (float)s;
