@@ -222,12 +222,14 @@ def _batched_leg(torch, pkg, units, warmup_units, k):
 
 def _elastic_leg(torch, pkg, steps, warmup, flush):
     """The homogeneous 3-D elastic workload (257^3 points, 4 x 4 x 4 patches, n_nb = 20, 20-point layers,
-    explosive + shear source, v1..v3 receivers on z = 0), FP32 with compensated updates, per-step events with an
-    L2 flush in between; per-kernel times from the library's events."""
+    explosive + shear source, v1..v3 receivers on z = 0), FP32 with compensated updates, tile shapes from the
+    library's autotuner, per-step events with an L2 flush in between; per-kernel times from the library's
+    events."""
     from synth import elastic3d_homogeneous
 
     w = elastic3d_homogeneous(precision="fp32_kahan")
     g = pkg.Grid.from_workloads([w])
+    tune = g.autotune(steps=2)
     g.step(warmup)
     g.sync()
     g.profile(True)
@@ -244,7 +246,7 @@ def _elastic_leg(torch, pkg, steps, warmup, flush):
             "value": value, "unit": UNIT, "ms_per_step": ms_step,
             "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items()},
             "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9),
-            "peak_kind": peak_kind_note(kind), "l2": "flushed between timed steps"}
+            "peak_kind": peak_kind_note(kind), "l2": "flushed between timed steps", "autotune": tune}
 
 
 def _adjoint_leg(steps):

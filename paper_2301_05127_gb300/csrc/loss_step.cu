@@ -327,8 +327,15 @@ static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A,
   LineGeom g;
   int logc, threads;
   const int kid = (k == 2) ? LOSS_KERNEL_ELASTIC_X : (k == 1 ? LOSS_KERNEL_ELASTIC_Y : LOSS_KERNEL_ELASTIC_Z);
-  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], h->chunk_log2[kid],
-                     h->tile_threads[kid]));
+  // Built-in FP32 shapes of the elastic passes (what the autotuner picks on the 257^3 and 193^3 grids): chunks of
+  // 8 unknowns on every axis, 128 threads per x block and 256 per y / z block.
+  int want_threads = h->tile_threads[kid], want_logc = h->chunk_log2[kid];
+  if (sizeof(T) == 4 && h->lines_per_block[kid] <= 0) {
+    if (want_threads <= 0) want_threads = k == 2 ? 128 : 256;
+    if (want_logc <= 0) want_logc = 3;
+  }
+  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], want_logc,
+                     want_threads));
   ElArgs<T> a{};
   a.g = g;
   a.tb = Tables{s.W[k], h->t32, h->t64};
