@@ -111,12 +111,25 @@ static int sig_of(int i, int j) {
   return LOSS_FIELD_S23;
 }
 
+// Built-in FP32 shape of the adjoint kernels (measured on the 193^3 gradient: 128 threads, chunks of 8, 4 % faster
+// than the line kernels' defaults); a shape set with loss_set_tile / loss_set_launch takes precedence.
+template <typename T>
+static int adj_threads(const loss_ctx* h) {
+  const int t = h->tile_threads[LOSS_KERNEL_ADJOINT];
+  return (t <= 0 && sizeof(T) == 4 && h->lines_per_block[LOSS_KERNEL_ADJOINT] <= 0) ? 128 : t;
+}
+template <typename T>
+static int adj_logc(const loss_ctx* h) {
+  const int c = h->chunk_log2[LOSS_KERNEL_ADJOINT];
+  return (c <= 0 && sizeof(T) == 4) ? 3 : c;
+}
+
 template <typename T>
 static loss_status_t launch_term(loss_ctx* h, Shot& s, int slot, AdjArgs<T>& a) {
   LineGeom g;
   int logc, threads;
   LOSS_TRY(line_geom(h, s, slot, s.sz, s.sy, &g, &logc, &threads, 4, 0, h->lines_per_block[LOSS_KERNEL_ADJOINT],
-                     h->chunk_log2[LOSS_KERNEL_ADJOINT], h->tile_threads[LOSS_KERNEL_ADJOINT]));
+                     adj_logc<T>(h), adj_threads<T>(h)));
   a.g = g;
   a.tb = Tables{s.W[slot], h->t32, h->t64};
   a.s3h = (T)(3.0 / s.h[slot]);
@@ -428,7 +441,7 @@ static loss_status_t derivative_adjoint_t(loss_ctx* h, Shot& s, int k, const T* 
   LineGeom geo;
   int logc, threads;
   LOSS_TRY(line_geom(h, s, k, sz, sy, &geo, &logc, &threads, 4, 0, h->lines_per_block[LOSS_KERNEL_ADJOINT],
-                     h->chunk_log2[LOSS_KERNEL_ADJOINT], h->tile_threads[LOSS_KERNEL_ADJOINT]));
+                     adj_logc<T>(h), adj_threads<T>(h)));
   AdjArgs<T> a{};
   a.g = geo;
   a.tb = Tables{s.W[k], h->t32, h->t64};

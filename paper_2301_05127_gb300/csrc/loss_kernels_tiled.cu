@@ -448,13 +448,13 @@ __device__ __forceinline__ SlowSet slow_set(int n, int nch, int W, bool src, int
 // One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY),
 // by a group of nt threads (whole warps; tid = index in the group).  Contains block-wide barriers: every thread of
 // the block calls it, each group for its own row (or with on = false: barriers only).
-template <bool KAHAN, class LAY>
+template <bool KAHAN, class LAY, class MIDB>
 __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int row,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
                                      const double* wd, float* dlf, const MemSeg& ms, const float* segB,
                                      const float* segA, float* PA, float* PB, const float* tabs, int tid, int nt,
-                                     bool on) {
+                                     bool on, const MIDB& midB) {
   const int n = t.n, np = n + 1;
   const int M = t.M;
   const int64_t rb = (int64_t)row * t.px;
@@ -584,6 +584,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       a.sigma[gi] = v;
     }
     __syncthreads();
+    midB();  // the B-only rows of this stage (kappa, d_z v3, sigma's compensation) are free from here on
   }
   const SlowSet SA = slow_set(n, nch, a.pml ? a.xA.width : 0, false, 0);
   if (act) {
@@ -741,29 +742,33 @@ __device__ __forceinline__ unsigned xp_row_bytes(const AcXArgs<float>& a, const 
   return narr * RB + (segs ? (a.do_B ? 2u : 1u) * (unsigned)ms.floats() * 4u : 0u);
 }
 // Bulk copies (one thread) of row `row` of one shot into a stage: six rows at S + k * stride and the two layer
-// segments, completing on *bar (whose expected bytes the caller has raised by xp_row_bytes).
+// segments, completing on *bar (whose expected bytes the caller has raised by xp_row_bytes).  part 1: the rows only
+// sub-step B reads (kappa, d_z v3, sigma's compensation, the phi_x segments); part 2: the others; 0: all.
 template <bool KAHAN>
 __device__ __forceinline__ void xp_issue(const AcXArgs<float>& a, const TileGeom& t, const MemSeg& ms, bool segs,
-                                         int row, float* S, int stride, float* seg0, float* seg1, uint64_t* bar) {
+                                         int row, float* S, int stride, float* seg0, float* seg1, uint64_t* bar,
+                                         int part = 0) {
   const int RW = (t.n + 1 + 3) & ~3;
   const unsigned RB = (unsigned)RW * 4u;
   const int64_t rb = (int64_t)row * t.px;
-  bulk_g2s(S, a.v1 + rb, RB, bar);
-  bulk_g2s(S + stride, a.sigma + rb, RB, bar);
-  if (a.do_B) {
+  if (part != 1) {
+    bulk_g2s(S, a.v1 + rb, RB, bar);
+    bulk_g2s(S + stride, a.sigma + rb, RB, bar);
+    if (KAHAN) bulk_g2s(S + 5 * stride, a.cv1 + rb, RB, bar);
+    if (segs) {
+      bulk_g2s(seg1, a.psix + rb, ms.SL * 4u, bar);
+      bulk_g2s(seg1 + ms.SL, a.psix + rb + ms.R0, ms.SR * 4u, bar);
+    }
+  }
+  if (part != 2 && a.do_B) {
     bulk_g2s(S + 2 * stride, a.kappa + rb, RB, bar);
     bulk_g2s(S + 3 * stride, a.tmp + rb, RB, bar);
     if (KAHAN) bulk_g2s(S + 4 * stride, a.csig + rb, RB, bar);
-  }
-  if (KAHAN) bulk_g2s(S + 5 * stride, a.cv1 + rb, RB, bar);
-  if (segs) {
-    if (a.do_B) {
+    if (segs) {
       bulk_g2s(seg0, a.phix + rb, ms.SL * 4u, bar);
       bulk_g2s(seg0 + ms.SL, a.phix + rb + ms.R0, ms.SR * 4u, bar);
       if (a.zB.in(row)) prefetch_l2(a.phiz + rb, RB);
     }
-    bulk_g2s(seg1, a.psix + rb, ms.SL * 4u, bar);
-    bulk_g2s(seg1 + ms.SL, a.psix + rb + ms.R0, ms.SR * 4u, bar);
   }
 }
 
@@ -803,11 +808,19 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
   float* TAB = base + L.TAB;
   xp_stage_shot(a, t, ms, segs, WS, TAB);  // loaded once
   __syncthreads();
-  auto issue = [&](int row, int st) {
-    mbar_expect_tx(&bar[st], xp_row_bytes<KAHAN>(a, t, ms, segs));
-    xp_issue<KAHAN>(a, t, ms, segs, row, base + (size_t)st * L.NA * L.RW, L.RW, segp(st, 0), segp(st, 1), &bar[st]);
+  // Copies of a row into a stage: part 1 arms the stage's barrier with the row's bytes (part 0: all at once).
+  auto issue = [&](int row, int st, int part) {
+    if (part != 2) mbar_expect_tx(&bar[st], xp_row_bytes<KAHAN>(a, t, ms, segs));
+    xp_issue<KAHAN>(a, t, ms, segs, row, base + (size_t)st * L.NA * L.RW, L.RW, segp(st, 0), segp(st, 1), &bar[st],
+                    part);
   };
-  if (threadIdx.x == 0 && (int)blockIdx.x < nrows) issue(blockIdx.x, 0);
+  // With sub-step B the rows only B reads are copied earlier: those of row + 2G go into the current stage as soon
+  // as B is done with it, the rest of a row at the start of the row before it.
+  const bool split = a.do_B != 0;
+  if (threadIdx.x == 0 && (int)blockIdx.x < nrows) {
+    issue(blockIdx.x, 0, 0);
+    if (split && (int)blockIdx.x + G < nrows) issue(blockIdx.x + G, 1, 1);
+  }
   unsigned parity[2] = {0u, 0u};
   int i = 0;
   for (int row = blockIdx.x; row < nrows; row += G, ++i) {
@@ -815,20 +828,29 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
     const bool more = row + G < nrows;
     if (threadIdx.x == 0 && more) {
       fence_proxy_async();
-      issue(row + G, st ^ 1);
+      issue(row + G, st ^ 1, split ? 2 : 0);
     }
     const bool ok = mbar_wait(&bar[st], parity[st], 1u << 24);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0) {  // let the copies in flight land (bounded) before the block leaves
         atomicExch(err, 1);
+        mbar_wait(&bar[st], parity[st], 1u << 24);
         if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], 1u << 24);
       }
       return;
     }
     parity[st] ^= 1u;
     float* S = base + (size_t)st * L.NA * L.RW;
+    const bool more2 = split && row + 2 * G < nrows;
+    auto midB = [&] {
+      if (threadIdx.x == 0 && more2) {
+        fence_proxy_async();
+        issue(row + 2 * G, st, 1);
+      }
+    };
     xrow<KAHAN>(a, t, mmagic, row, lay, S, S + L.RW, S + 2 * L.RW, S + 3 * L.RW, S + 4 * L.RW, S + 5 * L.RW,
-                base + L.O, rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB, threadIdx.x, blockDim.x, true);
+                base + L.O, rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB, threadIdx.x, blockDim.x, true,
+                midB);
     __syncthreads();
   }
 }
@@ -943,7 +965,7 @@ __global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ 
     float* PAg = base + L.PA + (size_t)g * 2 * q.pa;
     xrow<KAHAN>(d.a, d.t, d.mmagic, row, lay, S, S + q.RR, S + 2 * q.RR, S + 3 * q.RR, S + 4 * q.RR, S + 5 * q.RR,
                 base + L.O + (size_t)g * q.ocap, rpow, d.t.Wd, dlf + g * 65, ms, segp(st, 0, q, g), segp(st, 1, q, g),
-                PAg, PAg + q.pa, TAB, threadIdx.x - g * nt, nt, row < d.t.ncross);
+                PAg, PAg + q.pa, TAB, threadIdx.x - g * nt, nt, row < d.t.ncross, [] {});
     __syncthreads();
   }
 }
