@@ -78,6 +78,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x, ws, device):
+    """The largest x over the ranks of the process group (x itself for one process)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, points, ms_per_step):
+    """Whole-job grid-point updates per second: every rank advances its own replica of the workload, and the step
+    time is the slowest rank's."""
+    return ws * points / (ms_per_step * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,14 +314,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(x, ws, dev)
 
     w = acoustic2d_layered(precision="fp32_kahan")
     pts = w.points
@@ -328,9 +340,9 @@ def run_ours(args):
     prof_ms = _timed_steps(torch, g, args.steps, flush)
     kern = {k: g.profile_read(k) for k in KERNELS + ("gather",)}
     g.profile(False)
-    sum_ms = max_over_ranks(sum(step_ms))
+    sum_ms = slowest(sum(step_ms))
     ms_per_step = sum_ms / args.steps
-    value = ws * pts / (ms_per_step * 1e-3)
+    value = job_value(ws, pts, ms_per_step)
 
     # dominant kernel roofline
     dom = max(KERNELS, key=lambda k: kern[k][0])
@@ -350,7 +362,7 @@ def run_ours(args):
     g64.sync()
     n64 = max(1, min(args.steps, max(3, args.steps // 2)))
     ms64 = _timed_steps(torch, g64, n64, flush)
-    fp64_ms = max_over_ranks(sum(ms64)) / len(ms64)
+    fp64_ms = slowest(sum(ms64)) / len(ms64)
     # same number of steps as the FP32 run (timed and profiled passes) for the accuracy comparison
     if 2 * args.steps > len(ms64):
         g64.step(2 * args.steps - len(ms64))
@@ -383,7 +395,7 @@ def run_ours(args):
     ge.get_field(0, "sigma", out=host_out)
     e1.record()
     e1.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e_ms = slowest(e0.elapsed_time(e1))
     h2d = 3 * pts * 4
     d2h = pts * 4 + tr.nbytes
     ge.close()
@@ -404,7 +416,7 @@ def run_ours(args):
             "kernels_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in kern.items()},
             "kernels_frac_of_peak": {k: _alg_bytes_per_point(k, 4, True, False) * pts / (kern[k][0] / kern[k][1] * 1e-3)
                                      / (peak * 1e9) for k in KERNELS if kern[k][1]},
-            "fp64": {"value": ws * pts / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "unit": UNIT},
+            "fp64": {"value": job_value(ws, pts, fp64_ms), "ms_per_step": fp64_ms, "unit": UNIT},
             "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + 2 * args.steps},
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms},
