@@ -45,12 +45,17 @@ KERNEL_OF = {"acoustic_x": "k_xp", "acoustic_z": "k_tz<1", "acoustic_z2": "k_tz<
 
 
 def kernel_sources_digest():
+    """Digest of the kernel sources without comments and whitespace (a comment edit leaves the kernels as they
+    were captured)."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            code = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update("".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

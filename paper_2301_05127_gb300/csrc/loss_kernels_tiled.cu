@@ -1,15 +1,23 @@
-// sm_103a FP32 kernels of the 2-D acoustic step in the truncated-convolution form (loss_fir.cuh), on tiles of
-// one patch.
+// sm_103a FP32 kernels of the 2-D acoustic step in the truncated-convolution form (loss_fir.cuh).
 //
-// Every output point of the LOSS derivative depends only on the field within its own patch, the K positions
-// beyond each patch end (warm-up of the recursions) and the n_nb positions around the patch's two junctions
-// (PMBC sums).  A thread block therefore takes one patch of a bundle of lines plus a halo of H >= max(n_nb, K)
-// positions on each side; tiles are independent, so no block needs whole lines on chip:
-//   z tiles: 32 neighbouring x columns x one patch of z (one 128-byte row segment per z position; a warp is one
-//            chunk of C z positions for the 32 columns, so shared-memory accesses are conflict-free),
-// The step is three launches: the fused x kernel on whole rows (sub-step B with d_x v1 and the staged d_z v3, then
-// the x part of A with d_x sigma), Z1 (z part of A, d_z sigma) and Z2 (d_z v3 for the next step's B) on z tiles.
-// A z tile owns the positions [jM, jM + M) of its patch, and the last patch also the line's last point.
+// Every output point of the LOSS derivative depends only on:
+//   - the field within its own patch;
+//   - the K positions beyond each patch end (warm-up of the recursions);
+//   - the n_nb positions around the patch's two junctions (PMBC sums, here FP64 junction corrections).
+// So no block needs whole lines on chip:
+//   - z tiles (k_tz): 32 neighbouring x columns x one patch of z plus a halo of H = max(n_nb, K) positions on
+//     each side. There is one 128-byte row segment per z position, and a warp takes one chunk of C z positions
+//     for the 32 columns, so shared-memory accesses are conflict-free. A z tile owns the positions
+//     [jM, jM + M) of its patch; the last patch also owns the line's last point.
+//   - x rows (k_xp): one block per row at a time, persistent over rows, with the next row's arrays bulk-copied
+//     (TMA) into a second shared-memory stage while the current row is computed.
+// The step is three launches:
+//   - the fused x kernel on whole rows: sub-step B with d_x v1 and the staged d_z v3, then the x part of A with
+//     d_x sigma;
+//   - Z1: the z part of A, from d_z sigma;
+//   - Z2: d_z v3 for the next step's B.
+// The batched forms (k_xp_batch, k_tz_batch) advance the rows and tiles of many shots in one persistent launch
+// each, with the same per-row and per-tile arithmetic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
