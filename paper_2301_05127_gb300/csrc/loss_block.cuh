@@ -117,6 +117,29 @@ __device__ __forceinline__ void for_points(const LineGeom& g, const int64_t* lb,
 
 __device__ __forceinline__ int log2_pow2(int L) { return __ffs(L) - 1; }
 
+// Bulk L2 prefetch of a bundle's elements of narr arrays (null entries skipped), so that a later pointwise phase
+// finds them in L2: S flavour one segment of L elements per line position (when L elements are a multiple of 16
+// bytes), X flavour one padded row per line.  Segments stay within the padded rows.
+template <typename T, bool SFLAV>
+__device__ __forceinline__ void prefetch_bundle(const LineGeom& g, const int64_t* lb, int nvalid,
+                                                const T* const* arrs, int narr) {
+  const int np = g.n + 1;
+  if (SFLAV) {
+    const uint32_t sb = (uint32_t)(g.L * sizeof(T));
+    if ((sb & 15u) != 0) return;
+    for (int i = threadIdx.x; i < narr * np; i += blockDim.x) {
+      const T* base = arrs[i / np];
+      if (base) prefetch_l2(base + lb[0] + (int64_t)(i % np) * g.pstride, sb);
+    }
+  } else {
+    const uint32_t rb = (uint32_t)((np * sizeof(T) + 15) & ~(size_t)15);
+    for (int i = threadIdx.x; i < narr * nvalid; i += blockDim.x) {
+      const T* base = arrs[i / nvalid];
+      if (base) prefetch_l2(base + lb[i % nvalid], rb);
+    }
+  }
+}
+
 // Four consecutive elements starting at a 16-byte aligned address.
 __device__ __forceinline__ void ld4(const float* p, float (&r)[4]) {
   const float4 t = *reinterpret_cast<const float4*>(p);

@@ -74,6 +74,34 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
   const int p1 = g.p + 1;
   chunk_classes_init<T, C>(&cc, g.M, g.NC, a.tb.t32, a.tb.t64, a.minf);
   __syncthreads();
+  if (!SFLAV) {
+    // the arrays the pointwise phase reads, into L2 while the rows are staged and solved (one bulk prefetch per
+    // row; on the y / z bundles the per-position 32-byte segments cost more than they save, measured)
+    const T* pre[20];
+    int np_ = 0;
+    T* const* tt = a.tmp;
+    if (PASS == EL_BY) {
+      pre[np_++] = tt[1];
+    } else if (PASS == EL_BZ && a.do_B) {
+      const int fs[6] = {LOSS_FIELD_S11, LOSS_FIELD_S22, LOSS_FIELD_S12, LOSS_FIELD_S13, LOSS_FIELD_S23,
+                         LOSS_FIELD_S33};
+      pre[np_++] = tt[0], pre[np_++] = tt[1], pre[np_++] = tt[2], pre[np_++] = tt[3], pre[np_++] = tt[4];
+      pre[np_++] = a.lam, pre[np_++] = a.mu;
+      for (int f = 0; f < 6; ++f) {
+        pre[np_++] = a.fld[fs[f]];
+        if (KAHAN) pre[np_++] = a.cmp[fs[f]];
+      }
+    } else if (PASS == EL_AX) {
+      pre[np_++] = tt[5], pre[np_++] = tt[6], pre[np_++] = tt[7];
+    } else if (PASS == EL_AY) {
+      pre[np_++] = tt[5], pre[np_++] = tt[6], pre[np_++] = tt[7], pre[np_++] = a.b;
+      for (int f = LOSS_FIELD_V1; f <= LOSS_FIELD_V3; ++f) {
+        pre[np_++] = a.fld[f];
+        if (KAHAN) pre[np_++] = a.cmp[f];
+      }
+    }
+    prefetch_bundle<T, SFLAV>(g, cv.lb, nvalid, pre, np_);
+  }
   for (int s = 0; s < 3; ++s) stage_padded<T, SFLAV>(a.src[s], F[s], bun, g, cv.lb, nvalid, logL);
   cp_async_commit();
   cp_async_wait<0>();
