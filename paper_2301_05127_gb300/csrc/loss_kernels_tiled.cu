@@ -149,10 +149,22 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
     const int wl = 2 * t.Rd + 1;
     for (int i = threadIdx.x; i < 2 * wl; i += blockDim.x) ts.wsm[i] = t.Wd[(size_t)l * wl + i];
   }
-  for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
-    const int q = i >> 3, seg = i & 7;
+  // two copy groups: first the rows the junction sums read (2H + 1 around each patch end), then the others, so
+  // that the FP64 junction sums run while the rest of the tile streams in
+  const int jr = 2 * t.H + 1;
+  auto copy_row = [&](int q, int seg) {
     const int pos = zb + q;
     if (pos >= 0 && pos <= t.n) cp_async<16>(F + q * 32 + seg * 4, f + (int64_t)pos * t.px + x0 + seg * 4);
+  };
+  for (int i = threadIdx.x; i < 2 * jr * 8; i += blockDim.x) {
+    const int q = i >> 3, seg = i & 7;
+    copy_row(q < jr ? q : t.M + (q - jr), seg);
+  }
+  cp_async_commit();
+  for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
+    const int q = i >> 3, seg = i & 7;
+    if (q < jr || (q >= t.M && q < t.M + jr)) continue;
+    copy_row(q, seg);
   }
   if (MODE == 1) {
     for (int i = threadIdx.x; i < (t.M + 1) * 8; i += blockDim.x) {
@@ -165,11 +177,12 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
     }
   }
   cp_async_commit();
-  cp_async_wait<0>();
+  cp_async_wait<1>();
   __syncthreads();
   const ZBun bun{zb};
   const int nvalid = min(32, t.ncross - x0);
   tile_junctions_z(F, bun, nvalid, l, t, nwj, ts.wsm, ts.jpart, ts.dl);
+  cp_async_wait<0>();
   __syncthreads();
   const int col = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;
