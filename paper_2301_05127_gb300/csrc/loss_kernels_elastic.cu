@@ -102,9 +102,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
     }
     prefetch_bundle<T, SFLAV>(g, cv.lb, nvalid, pre, np_);
   }
-  for (int s = 0; s < 3; ++s) stage_padded<T, SFLAV>(a.src[s], F[s], bun, g, cv.lb, nvalid, logL);
+  // the first field in a copy group of its own: its PMBC sums and solve run while the other two stream in
+  stage_padded<T, SFLAV>(a.src[0], F[0], bun, g, cv.lb, nvalid, logL);
   cp_async_commit();
-  cp_async_wait<0>();
+  for (int s = 1; s < 3; ++s) stage_padded<T, SFLAV>(a.src[s], F[s], bun, g, cv.lb, nvalid, logL);
+  cp_async_commit();
+  cp_async_wait<1>();
   __syncthreads();
   auto derive = [&](int s) {
     pmbc_phi<T, 16>(F[s], bun, g.L, nvalid, g.n, g.p, g.M, g.n_nb, a.tb.W, cv.phi);
@@ -112,7 +115,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
     solve_bundle<T, C, SFLAV>(F[s], O[s], cv.sA, &cc, bun, wm, nvalid, g.M, a.tb.t32, a.tb.t64, a.minf, RhsD1{},
                               BndPhi<T>{cv.phi, p1});
   };
-  for (int s = 0; s < 3; ++s) derive(s);
+  derive(0);
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int s = 1; s < 3; ++s) derive(s);
   const T dt = a.dt, ta = a.acoef;
   T* const* t = a.tmp;
   if (PASS == EL_BX) {
