@@ -382,28 +382,32 @@ def run_ours(args):
     adjoint = _adjoint_leg(steps=60) if not args.no_batched else None
 
     # --- end to end through the public API with host buffers ---------------------------------------------
-    ge = pkg.Grid.from_workloads([w])
+    # three runs on fresh handles (the timed region holds host round trips: the median is reported)
     shape = w.shape
     host_in = [torch.zeros(shape, dtype=torch.float32).pin_memory() for _ in range(3)]
     host_in[0].copy_(torch.from_numpy(np.zeros(shape, np.float32)))
     host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
-    ge.step(1)  # graph of kernels warm (stagger prologue paid in the timed region below anyway)
-    ge.sync()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for f, hb in zip(("sigma", "v1", "v3"), host_in):
-        ge.set_field(0, f, hb)
-    ge.step(args.steps)
-    tr = ge.record(0)["_all"]
-    ge.get_field(0, "sigma", out=host_out)
-    e1.record()
-    e1.synchronize()
-    e2e_ms = slowest(e0.elapsed_time(e1))
+    e2e_runs = []
+    for _ in range(3):
+        ge = pkg.Grid.from_workloads([w])
+        ge.step(1)  # kernels loaded and tables built; the staggered start is paid in the timed region anyway
+        ge.sync()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for f, hb in zip(("sigma", "v1", "v3"), host_in):
+            ge.set_field(0, f, hb)
+        ge.step(args.steps)
+        tr = ge.record(0)["_all"]
+        ge.get_field(0, "sigma", out=host_out)
+        e1.record()
+        e1.synchronize()
+        e2e_runs.append(slowest(e0.elapsed_time(e1)))
+        ge.close()
+    e2e_ms = sorted(e2e_runs)[1]
     h2d = 3 * pts * 4
     d2h = pts * 4 + tr.nbytes
-    ge.close()
 
     out = None
     if rank == 0:
@@ -424,7 +428,7 @@ def run_ours(args):
             "fp64": {"value": job_value(ws, pts, fp64_ms), "ms_per_step": fp64_ms, "unit": UNIT},
             "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + 2 * args.steps},
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                    "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms},
+                    "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms, "runs_ms": e2e_runs},
             "batched": batched,
             "elastic": elastic,
             "adjoint": adjoint,
