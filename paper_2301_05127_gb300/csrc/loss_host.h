@@ -228,7 +228,7 @@ cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int 
 template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
                       cudaStream_t st);
-size_t tile_smem_z(const TileGeom& t, int mode);
+size_t tile_smem_z(const TileGeom& t, int mode, int logc);
 size_t xp_smem(const TileGeom& t, bool kahan);
 int xp_rows_per_unit(int n, int threads);
 XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& rs, bool kahan);

@@ -87,36 +87,58 @@ __device__ void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, i
   }
 }
 
-// e on the chunk [p0, p0 + len) of line l inside the patch starting at z0 (len <= C + 1).
-template <int C, class BUN>
-__device__ __forceinline__ void tile_chunk(const float* __restrict__ F, const BUN& bun, int l, int p0, int len,
-                                           int z0, const TileGeom& t, const float* __restrict__ dl,
-                                           const float* __restrict__ rpow, float (&e)[C + 1]) {
-  constexpr int K = FirLen<float>::K;
-  float fv[C + 1];
+// Warm-up partial sums of a chunk's first C values: pa = sum_j r^(C-1-j) f_j (its part of the left sums of the
+// chunks after it) and pb = sum_j r^j f_j (its part of the right sums of the chunks before it), in the Horner order
+// of fir_left / fir_right.
+template <int C>
+__device__ __forceinline__ void chunk_partials(const float (&f)[C + 1], float r, float& pa, float& pb) {
+  pa = 0.0f;
+  pb = 0.0f;
 #pragma unroll
-  for (int j = 0; j <= C; ++j)
-    if (j < len) fv[j] = F[bun.at(l, p0 + j)];
-  float s = fir_left<float, K>(F, bun, l, p0, t.n, t.r);
+  for (int j = 0; j < C; ++j) pa = f[j] + r * pa;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) pb = f[j] + r * pb;
+}
+
+// e on the chunk [p0, p0 + len) of line l inside the patch starting at z0 (len <= C + 1), from its values fv and
+// the warm-up sums sL = L_{p0} and qR = R_{p0 + len - 1} (fir_left / fir_right, or the neighbours' partial sums).
+template <int C>
+__device__ __forceinline__ void tile_chunk_e(const float (&fv)[C + 1], int p0, int len, int z0, const TileGeom& t,
+                                             const float* __restrict__ dl, const float* __restrict__ rpow, float sL,
+                                             float qR, float (&e)[C + 1]) {
+  float s = sL;
 #pragma unroll
   for (int j = 0; j <= C; ++j)
     if (j < len) {
       e[j] = s;
       s = fv[j] + t.r * s;
     }
-  float q = fir_right<float, K>(F, bun, l, p0 + len - 1, t.n, t.r);
+  float q = qR;
 #pragma unroll
   for (int j = C; j >= 0; --j)
     if (j < len) {
       e[j] = t.a * (q - e[j]);
       q = fv[j] + t.r * q;
     }
+  // patch corrections; r^d runs along the chunk by multiplication from the table value at its near end (0 beyond
+  // the table)
   const float DT = dl[0], DB = dl[1];
   const float A = (DT - t.rho * DB) * t.inv, B = (DB - t.rho * DT) * t.inv;
   const int d0 = p0 - z0;
+  float qa = rpow[min(d0, kFirPow - 1)];                  // r^(d0 + j)
+  float qb = rpow[min(t.M - d0 - (len - 1), kFirPow - 1)];  // r^(M - d0 - j), from j = len - 1 down
 #pragma unroll
   for (int j = 0; j <= C; ++j)
-    if (j < len) e[j] += A * rpow[min(d0 + j, kFirPow - 1)] + B * rpow[min(t.M - d0 - j, kFirPow - 1)];
+    if (j < len) {
+      e[j] += A * qa;
+      qa *= t.r;
+    }
+#pragma unroll
+  for (int j = C; j >= 0; --j)
+    if (j < len) {
+      e[j] += B * qb;
+      qb *= t.r;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -187,12 +209,40 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
   const int col = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;
   const int p0 = z0 + c * C;
-  int len = min(C, z0 + t.M - p0);
-  if (len <= 0) return;                // warps beyond the patch (a batched block sized for a longer patch)
-  if (last && p0 + len == t.n) ++len;  // the line's last point
-  if (col >= nvalid) return;
+  int len = min(C, z0 + t.M - p0);     // len <= 0: warps beyond the patch (a batched block sized for a longer one)
+  const int lenx = len + ((len > 0 && last && p0 + len == t.n) ? 1 : 0);  // with the line's last point
+  // the warm-up sums of K = W C positions come from the W neighbouring chunks when they are whole chunks of this
+  // patch, else directly from the tile (its halo reaches K beyond the patch)
+  constexpr int W = FirLen<float>::K / C;
+  float* PA = SV + (MODE == 1 ? 2 * (t.M + 1) * 32 : 0);  // [chunk][32]: partial sums, after the staged rows
+  float* PB = PA + ((t.M + C - 1) / C) * 32;
+  float fv[C + 1];
+  const bool mine = len > 0 && col < nvalid;
+  if (mine) {
+#pragma unroll
+    for (int j = 0; j <= C; ++j)
+      if (j < lenx) fv[j] = F[bun.at(col, p0 + j)];
+    if (len == C) chunk_partials<C>(fv, t.r, PA[c * 32 + col], PB[c * 32 + col]);
+  }
+  __syncthreads();
+  if (!mine) return;
+  len = lenx;
+  const float rC = ts.rpow[C];
+  float sL, qR;
+  if (c >= W) {
+    sL = PA[(c - 1) * 32 + col];
+    if (W == 2) sL += rC * PA[(c - 2) * 32 + col];
+  } else {
+    sL = fir_left<float, FirLen<float>::K>(F, bun, col, p0, t.n, t.r);
+  }
+  if (len == C && (c + W + 1) * C <= t.M) {
+    qR = PB[(c + 1) * 32 + col];
+    if (W == 2) qR += rC * PB[(c + 2) * 32 + col];
+  } else {
+    qR = fir_right<float, FirLen<float>::K>(F, bun, col, p0 + len - 1, t.n, t.r);
+  }
   float e[C + 1];
-  tile_chunk<C>(F, bun, col, p0, len, z0, t, ts.dl + 2 * col, ts.rpow, e);
+  tile_chunk_e<C>(fv, p0, len, z0, t, ts.dl + 2 * col, ts.rpow, sL, qR, e);
   const int64_t base = x0 + col;
 #pragma unroll
   for (int j = 0; j <= C; ++j) {
@@ -993,9 +1043,13 @@ __global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ 
 
 // ---------------------------------------------------------------------------------------------------------------
 // Host side.
-size_t tile_smem_z(const TileGeom& t, int mode) {
+// Dynamic shared memory of a z tile: the rows, (Z1) the own rows of v3 and its compensation, and two partial sums
+// per chunk (2^logc positions) and column.
+size_t tile_smem_z(const TileGeom& t, int mode, int logc) {
   const int rows = t.M + 2 * t.H + 1;
-  return (size_t)rows * 32 * 4 + (mode == 1 ? (size_t)2 * (t.M + 1) * 32 * 4 : 0);
+  const int C = 1 << logc;
+  return (size_t)rows * 32 * 4 + (mode == 1 ? (size_t)2 * (t.M + 1) * 32 * 4 : 0) +
+         (size_t)2 * ((t.M + C - 1) / C) * 32 * 4;
 }
 template <class K>
 static cudaError_t tile_launch(K kern, int grid, int threads, size_t smem, cudaStream_t st, void** argv) {
@@ -1011,7 +1065,7 @@ cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int 
   TileGeom tt = t;
   void* argv[] = {&aa, &tt};
   const int grid = t.ntl * t.p;
-  const size_t smem = tile_smem_z(t, mode);
+  const size_t smem = tile_smem_z(t, mode, logc);
   if (logc == 3) {
     if (mode == 1) return tile_launch(k_tz<1, KAHAN, 3>, grid, threads, smem, st, argv);
     return tile_launch(k_tz<2, KAHAN, 3>, grid, threads, smem, st, argv);

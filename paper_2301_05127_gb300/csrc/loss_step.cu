@@ -714,7 +714,7 @@ static loss_status_t conv_tables(loss_ctx* h) {
       const TileGeom tz = tile_geom(s, 0, &thr, zlc[m]);
       zs[m * S + i] = TzShot{ac_z_args<float>(h, s, LineGeom{}, m == 0 ? s.d.dt : 0.0, 0), tz, thr >> 5, 0};
       zthreads[m] = std::max(zthreads[m], thr);
-      zsm[m] = std::max(zsm[m], tile_smem_z(tz, m + 1));
+      zsm[m] = std::max(zsm[m], tile_smem_z(tz, m + 1, zlc[m]));
       if (m == 0) zt0[i + 1] = zt0[i] + tz.ntl * tz.p;
     }
   }
