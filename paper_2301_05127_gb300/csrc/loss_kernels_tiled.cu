@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/loss.h"
@@ -553,73 +554,79 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     xf_junctions<8>(V, lay.bun, t, wd, dlf, tid, nt, on);
     __syncthreads();
     if (act) {
-      float e[9];
-      xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
-      const int ob = SB.ordinal(c);
-      if (ob >= 0) {
+      // one body per chunk length (8, or 9 for the chunk ending at n), so that the loops carry no predicates
+      auto chunkB = [&](auto np) {
+        constexpr int len = decltype(np)::value;
+        float e[9];
+        xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
+        const int ob = SB.ordinal(c);
+        if (ob >= 0) {
 #pragma unroll
-        for (int j = 0; j < 9; ++j)
-          if (j < len) O[9 * ob + j] = t.s3h * e[j];
-      } else {
-        float sg[9], cs[9], kp[9], gz[9], iz[9];
-        {
-          float v8[8];
-          lay.eight(D, c, v8);
+          for (int j = 0; j < 9; ++j)
+            if (j < len) O[9 * ob + j] = t.s3h * e[j];
+        } else {
+          float sg[9], cs[9], kp[9], gz[9], iz[9];
+          {
+            float v8[8];
+            lay.eight(D, c, v8);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) sg[j] = v8[j];
-          lay.eight(SK, c, v8);
+            for (int j = 0; j < 8; ++j) sg[j] = v8[j];
+            lay.eight(SK, c, v8);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) kp[j] = v8[j];
-          lay.eight(ST, c, v8);
+            for (int j = 0; j < 8; ++j) kp[j] = v8[j];
+            lay.eight(ST, c, v8);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) gz[j] = v8[j];
-          if (KAHAN) {
-            lay.eight(SC, c, v8);
+            for (int j = 0; j < 8; ++j) gz[j] = v8[j];
+            if (KAHAN) {
+              lay.eight(SC, c, v8);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) cs[j] = v8[j];
+              for (int j = 0; j < 8; ++j) cs[j] = v8[j];
+            }
+            if (len > 8) {
+              const int k8 = lay.chunk(c + 1);
+              sg[8] = D[k8], kp[8] = SK[k8], gz[8] = ST[k8];
+              if (KAHAN) cs[8] = SC[k8];
+            }
           }
-          if (len > 8) {
-            const int k8 = lay.chunk(c + 1);
-            sg[8] = D[k8], kp[8] = SK[k8], gz[8] = ST[k8];
-            if (KAHAN) cs[8] = SC[k8];
+          if (zlay) {  // z memory variable of this row (PmlAxis::step, vectorised)
+            float pz[9];
+            load_run<8>(a.phiz + rb + p0, len, pz);
+            const int n1z = a.zB.n + 1;
+            const float T0 = a.zB.tab[row], T1 = a.zB.tab[n1z + row], T2 = a.zB.tab[2 * n1z + row],
+                        T3 = a.zB.tab[3 * n1z + row];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+              const float m1 = T0 * pz[j] - T1 * gz[j];
+              iz[j] = T2 * (m1 - pz[j]) - T3 * gz[j];
+              pz[j] = m1;
+            }
+            store_run<8>(a.phiz + rb + p0, len, pz);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) iz[j] = -a.dt * gz[j];
           }
-        }
-        if (zlay) {  // z memory variable of this row (PmlAxis::step, vectorised)
-          float pz[9];
-          load_run<8>(a.phiz + rb + p0, len, pz);
-          const int n1z = a.zB.n + 1;
-          const float T0 = a.zB.tab[row], T1 = a.zB.tab[n1z + row], T2 = a.zB.tab[2 * n1z + row],
-                      T3 = a.zB.tab[3 * n1z + row];
 #pragma unroll
           for (int j = 0; j < 9; ++j) {
-            const float m1 = T0 * pz[j] - T1 * gz[j];
-            iz[j] = T2 * (m1 - pz[j]) - T3 * gz[j];
-            pz[j] = m1;
+            if (j >= len) break;
+            const float delta = kp[j] * (-a.dt * (t.s3h * e[j]) + iz[j]);
+            float v = sg[j];
+            if (KAHAN) {
+              float cc = cs[j];
+              kahan_add(v, cc, delta);
+              cs[j] = cc;
+            } else {
+              v += delta;
+            }
+            sg[j] = v;
           }
-          store_run<8>(a.phiz + rb + p0, len, pz);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 9; ++j) iz[j] = -a.dt * gz[j];
+          lay.store8(D, c, sg);
+          if (len > 8) D[lay.chunk(c + 1)] = sg[8];
+          store_run<8>(a.sigma + rb + p0, len, sg);
+          if (KAHAN) store_run<8>(a.csig + rb + p0, len, cs);
         }
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          if (j >= len) break;
-          const float delta = kp[j] * (-a.dt * (t.s3h * e[j]) + iz[j]);
-          float v = sg[j];
-          if (KAHAN) {
-            float cc = cs[j];
-            kahan_add(v, cc, delta);
-            cs[j] = cc;
-          } else {
-            v += delta;
-          }
-          sg[j] = v;
-        }
-        lay.store8(D, c, sg);
-        if (len > 8) D[lay.chunk(c + 1)] = sg[8];
-        store_run<8>(a.sigma + rb + p0, len, sg);
-        if (KAHAN) store_run<8>(a.csig + rb + p0, len, cs);
-      }
+      };
+      if (len == 9) chunkB(std::integral_constant<int, 9>{});
+      else chunkB(std::integral_constant<int, 8>{});
     }
     __syncthreads();
     const int nsB = 9 * SB.count();
@@ -666,49 +673,54 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   xf_junctions<8>(D, lay.bun, t, wd, dlf, tid, nt, on);
   __syncthreads();
   if (act) {
-    float e[9];
-    xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
-    const int oa = SA.ordinal(c);
-    if (oa >= 0) {
+    auto chunkA = [&](auto np) {
+      constexpr int len = decltype(np)::value;
+      float e[9];
+      xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
+      const int oa = SA.ordinal(c);
+      if (oa >= 0) {
 #pragma unroll
-      for (int j = 0; j < 9; ++j)
-        if (j < len) O[9 * oa + j] = t.s3h * e[j];
-    } else {
-      float vv[9], cs[9], bb[9];
-      {
-        float v8[8];
-        lay.eight(V, c, v8);
+        for (int j = 0; j < 9; ++j)
+          if (j < len) O[9 * oa + j] = t.s3h * e[j];
+      } else {
+        float vv[9], cs[9], bb[9];
+        {
+          float v8[8];
+          lay.eight(V, c, v8);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) vv[j] = v8[j];
-        if (KAHAN) {
-          lay.eight(SV, c, v8);
+          for (int j = 0; j < 8; ++j) vv[j] = v8[j];
+          if (KAHAN) {
+            lay.eight(SV, c, v8);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) cs[j] = v8[j];
+            for (int j = 0; j < 8; ++j) cs[j] = v8[j];
+          }
+          if (len > 8) {
+            vv[8] = V[lay.chunk(c + 1)];
+            if (KAHAN) cs[8] = SV[lay.chunk(c + 1)];
+          }
         }
-        if (len > 8) {
-          vv[8] = V[lay.chunk(c + 1)];
-          if (KAHAN) cs[8] = SV[lay.chunk(c + 1)];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) bb[j] = (a.b && j < len) ? a.b[rb + p0 + j] : a.b0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          if (j >= len) break;
+          const float delta = bb[j] * (-a.acoef * (t.s3h * e[j]));
+          float v = vv[j];
+          if (KAHAN) {
+            float cc = cs[j];
+            kahan_add(v, cc, delta);
+            cs[j] = cc;
+          } else {
+            v += delta;
+          }
+          vv[j] = v;
         }
+        store_run<8>(a.v1 + rb + p0, len, vv);
+        if (KAHAN) store_run<8>(a.cv1 + rb + p0, len, cs);
       }
-#pragma unroll
-      for (int j = 0; j < 9; ++j) bb[j] = (a.b && j < len) ? a.b[rb + p0 + j] : a.b0;
-#pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        if (j >= len) break;
-        const float delta = bb[j] * (-a.acoef * (t.s3h * e[j]));
-        float v = vv[j];
-        if (KAHAN) {
-          float cc = cs[j];
-          kahan_add(v, cc, delta);
-          cs[j] = cc;
-        } else {
-          v += delta;
-        }
-        vv[j] = v;
-      }
-      store_run<8>(a.v1 + rb + p0, len, vv);
-      if (KAHAN) store_run<8>(a.cv1 + rb + p0, len, cs);
-    }
+    };
+    if (len == 9) chunkA(std::integral_constant<int, 9>{});
+    else chunkA(std::integral_constant<int, 8>{});
   }
   __syncthreads();
   const int nsA = 9 * SA.count();
