@@ -242,40 +242,46 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
   } else {
     qR = fir_right<float, FirLen<float>::K>(F, bun, col, p0 + len - 1, t.n, t.r);
   }
-  float e[C + 1];
-  tile_chunk_e<C>(fv, p0, len, z0, t, ts.dl + 2 * col, ts.rpow, sL, qR, e);
-  const int64_t base = x0 + col;
+  // one body for whole chunks (len == C, a compile-time count) and one for the others
+  auto finish = [&](auto lc) {
+    const int len = decltype(lc)::value > 0 ? decltype(lc)::value : lenx;
+    float e[C + 1];
+    tile_chunk_e<C>(fv, p0, len, z0, t, ts.dl + 2 * col, ts.rpow, sL, qR, e);
+    const int64_t base = x0 + col;
 #pragma unroll
-  for (int j = 0; j <= C; ++j) {
-    if (j >= len) break;
-    const int pos = p0 + j;
-    const int64_t gi = (int64_t)pos * t.px + base;
-    const float gz = t.s3h * e[j];
-    if (MODE == 2) {
-      a.tmp[gi] = gz;
-      continue;
+    for (int j = 0; j <= C; ++j) {
+      if (j >= len) break;
+      const int pos = p0 + j;
+      const int64_t gi = (int64_t)pos * t.px + base;
+      const float gz = t.s3h * e[j];
+      if (MODE == 2) {
+        a.tmp[gi] = gz;
+        continue;
+      }
+      const float bb = a.b ? a.b[gi] : a.b0;
+      float inc;
+      if (a.pml && a.zA.in(pos)) {
+        const float ih = a.dlt ? a.zA.half(a.psiz, gi, pos, gz) : 0.0f;
+        inc = a.zA.step(a.psiz, gi, pos, gz);
+        if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
+      } else {
+        inc = -a.acoef * gz;
+      }
+      const float delta = bb * inc;
+      const int k = (pos - z0) * 32 + col;
+      float v = SV[k];
+      if (KAHAN) {
+        float cc = SC[k];
+        kahan_add(v, cc, delta);
+        a.cv3[gi] = cc;
+      } else {
+        v += delta;
+      }
+      a.v3[gi] = v;
     }
-    const float bb = a.b ? a.b[gi] : a.b0;
-    float inc;
-    if (a.pml && a.zA.in(pos)) {
-      const float ih = a.dlt ? a.zA.half(a.psiz, gi, pos, gz) : 0.0f;
-      inc = a.zA.step(a.psiz, gi, pos, gz);
-      if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
-    } else {
-      inc = -a.acoef * gz;
-    }
-    const float delta = bb * inc;
-    const int k = (pos - z0) * 32 + col;
-    float v = SV[k];
-    if (KAHAN) {
-      float cc = SC[k];
-      kahan_add(v, cc, delta);
-      a.cv3[gi] = cc;
-    } else {
-      v += delta;
-    }
-    a.v3[gi] = v;
-  }
+  };
+  if (len == C) finish(std::integral_constant<int, C>{});
+  else finish(std::integral_constant<int, 0>{});
 }
 
 // One shot: one block per tile, 32 x ceil(M / C) threads.
@@ -520,7 +526,7 @@ __device__ __forceinline__ SlowSet slow_set(int n, int nch, int W, bool src, int
 // One row of the fused x step (sub-step B, then the x part of A) from rows already in shared memory (layout LAY),
 // by a group of nt threads (whole warps; tid = index in the group).  Contains block-wide barriers: every thread of
 // the block calls it, each group for its own row (or with on = false: barriers only).
-template <bool KAHAN, class LAY, class MIDB>
+template <bool KAHAN, bool SPLITLEN, class LAY, class MIDB>
 __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int row,
                                      const LAY& lay, float* V, float* D, const float* SK, const float* ST,
                                      const float* SC, const float* SV, float* O, const float* rpow,
@@ -554,9 +560,11 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
     xf_junctions<8>(V, lay.bun, t, wd, dlf, tid, nt, on);
     __syncthreads();
     if (act) {
-      // one body per chunk length (8, or 9 for the chunk ending at n), so that the loops carry no predicates
+      // SPLITLEN: one body per chunk length (8, or 9 for the chunk ending at n), so that the loops carry no
+      // predicates; else one body for both (smaller code, for the register-bound batched kernel)
+      const int len_rt = len;
       auto chunkB = [&](auto np) {
-        constexpr int len = decltype(np)::value;
+        const int len = decltype(np)::value > 0 ? decltype(np)::value : len_rt;
         float e[9];
         xf_chunk(V, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
         const int ob = SB.ordinal(c);
@@ -625,7 +633,8 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
           if (KAHAN) store_run<8>(a.csig + rb + p0, len, cs);
         }
       };
-      if (len == 9) chunkB(std::integral_constant<int, 9>{});
+      if (!SPLITLEN) chunkB(std::integral_constant<int, 0>{});
+      else if (len == 9) chunkB(std::integral_constant<int, 9>{});
       else chunkB(std::integral_constant<int, 8>{});
     }
     __syncthreads();
@@ -673,8 +682,9 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
   xf_junctions<8>(D, lay.bun, t, wd, dlf, tid, nt, on);
   __syncthreads();
   if (act) {
+    const int len_rt = len;
     auto chunkA = [&](auto np) {
-      constexpr int len = decltype(np)::value;
+      const int len = decltype(np)::value > 0 ? decltype(np)::value : len_rt;
       float e[9];
       xf_chunk(D, lay, c, len, t, M, mmagic, dlf, rpow, PA, PB, e);
       const int oa = SA.ordinal(c);
@@ -719,7 +729,8 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
         if (KAHAN) store_run<8>(a.cv1 + rb + p0, len, cs);
       }
     };
-    if (len == 9) chunkA(std::integral_constant<int, 9>{});
+    if (!SPLITLEN) chunkA(std::integral_constant<int, 0>{});
+    else if (len == 9) chunkA(std::integral_constant<int, 9>{});
     else chunkA(std::integral_constant<int, 8>{});
   }
   __syncthreads();
@@ -931,7 +942,7 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
         issue(row + 2 * G, st, 1);
       }
     };
-    xrow<KAHAN>(a, t, mmagic, row, lay, S, S + L.RW, S + 2 * L.RW, S + 3 * L.RW, S + 4 * L.RW, S + 5 * L.RW,
+    xrow<KAHAN, true>(a, t, mmagic, row, lay, S, S + L.RW, S + 2 * L.RW, S + 3 * L.RW, S + 4 * L.RW, S + 5 * L.RW,
                 base + L.O, rpow, WS, dlf, ms, segp(st, 0), segp(st, 1), PA, PB, TAB, threadIdx.x, blockDim.x, true,
                 midB);
     __syncthreads();
@@ -1046,7 +1057,7 @@ __global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ 
     const int row = (u - d.unit0) * q.R + g;
     float* S = base + (size_t)st * L.NA * L.RW + (size_t)g * q.RW;
     float* PAg = base + L.PA + (size_t)g * 2 * q.pa;
-    xrow<KAHAN>(d.a, d.t, d.mmagic, row, lay, S, S + q.RR, S + 2 * q.RR, S + 3 * q.RR, S + 4 * q.RR, S + 5 * q.RR,
+    xrow<KAHAN, false>(d.a, d.t, d.mmagic, row, lay, S, S + q.RR, S + 2 * q.RR, S + 3 * q.RR, S + 4 * q.RR, S + 5 * q.RR,
                 base + L.O + (size_t)g * q.ocap, rpow, d.t.Wd, dlf + g * 65, ms, segp(st, 0, q, g), segp(st, 1, q, g),
                 PAg, PAg + q.pa, TAB, threadIdx.x - g * nt, nt, row < d.t.ncross, [] {});
     __syncthreads();
