@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(1024) k_tz(AcZArgs<float> a, TileGeom t) {
 }
 
 // All shots in one persistent launch: tiles tile0[s] .. tile0[s + 1] - 1 belong to shot s; the block size is the
-// largest of the shots' own (at most 512: patches of at most 256 points).
+// largest of the shots' own (at most 512 threads).
 template <int MODE, bool KAHAN, int LOGC>
 __global__ void __launch_bounds__(512) k_tz_batch(const TzShot* __restrict__ tab, const int* __restrict__ tile0,
                                                    int nshots, int ntiles) {
