@@ -235,12 +235,14 @@ loss_status_t loss_set_launch(loss_handle_t handle, int32_t kernel, int32_t line
  * values out of range. */
 loss_status_t loss_set_tile(loss_handle_t handle, int32_t kernel, int32_t threads_per_block, int32_t chunk_log2);
 
-/* Schedule of loss_step (spec batching pattern; the paper's MPI design runs one process per patch instead).
- * batched != 0 (the default): a handle whose shots are all 2-D acoustic grids of one precision advances them
- * together, each step being one persistent launch of the x kernel and one of the z kernel over the tiles of all
- * shots (a tile = one bundle of whole lines of one shot), one launch per receiver phase and a clock tick.  The
- * source amplitude and the trace row of each step are read from per-shot device counters, so the launches of
- * every step are identical.  graph_steps > 0: such handles (also with a single shot) capture graph_steps steps
+/* Schedule of loss_step: the batched multi-shot schedule (the paper's MPI design runs one process per patch
+ * instead).  batched != 0 (the default): a handle whose shots are all 2-D acoustic grids of one precision advances
+ * them together, each step being one persistent launch per kernel over the work of all shots, one launch per
+ * receiver phase and a clock tick.  The kernels are those of the per-shot step: with the truncated-convolution
+ * family (FP32, when every shot qualifies) the x kernel over row units of all shots, then Z1 and Z2 over the z
+ * tiles of all shots; otherwise the line kernels, x and z over bundles of whole lines.  The source amplitude and
+ * the trace row of each step are read from per-shot device counters, so the launches of every step are
+ * identical.  graph_steps > 0: such handles (also with a single shot) capture graph_steps steps
  * once in a CUDA graph and replay it (the remainder of a loss_step call runs as plain launches); the graph is
  * captured again when shapes, buffers or the shot set change.  Results are those of the per-shot schedule.
  * Other handles (3-D elastic) always use per-shot launches.  Per-kernel timing (loss_profile) is not available
@@ -265,8 +267,8 @@ typedef struct {
   double ms;                 /* mean device time of one launch of the chosen shape */
 } loss_tune_entry_t;
 
-/* Project-written autotuner (spec batching pattern): times every candidate tile shape (threads per block
- * 128..1024, chunk_log2 3 or 4; for the convolution kernels the z chunk of Z1 and Z2) of each kernel family the
+/* Project-written autotuner (for the batched multi-shot schedule): times every candidate tile shape (threads per
+ * block 128..1024, chunk_log2 3 or 4; for the convolution kernels the z chunk of Z1 and Z2) of each kernel family the
  * handle's time step uses, on a scratch copy of the handle (same grids, models, absorbing layers, kernel family
  * and schedule; zero fields), with `steps` timed steps per candidate
  * after one warm-up step, and applies the fastest shape of each family to the handle (loss_set_tile).  The
