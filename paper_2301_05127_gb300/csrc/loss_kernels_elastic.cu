@@ -44,19 +44,18 @@ __device__ __forceinline__ T effA(const ElArgs<T>& a, int term, int64_t gi, int 
   return xf;
 }
 
+// u += delta in registers (compensated with c when KAHAN); the caller loads and stores.
 template <typename T, bool KAHAN>
-__device__ __forceinline__ T upd(T* f, T* c, int64_t gi, T delta) {
-  T u = f[gi];
+__device__ __forceinline__ void upd_r(T& u, T& c, T delta) {
   if constexpr (KAHAN) {
-    float cc = c[gi];
+    float cc = c;
     kahan_add(u, cc, delta);
-    c[gi] = cc;
+    c = cc;
   } else {
     u += delta;
   }
-  f[gi] = u;
-  return u;
 }
+
 
 template <typename T, int LOGC, bool SFLAV, int PASS, bool KAHAN>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a) {
@@ -131,9 +130,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
   } else if (PASS == EL_BY) {
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
-      t[1][gi] += eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
-      t[3][gi] = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
-      t[4][gi] = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+      const T t1 = t[1][gi];  // loaded before any store (see EL_BZ)
+      const T x0 = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
+      const T x1 = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
+      const T x2 = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+      t[1][gi] = t1 + x0;
+      t[3][gi] = x1;
+      t[4][gi] = x2;
     });
   } else if (PASS == EL_BZ) {
     if (a.do_B) {
@@ -141,15 +144,25 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
       const int x0 = (blockIdx.x - outer * g.nxb) * g.L;
       for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
         const int k = bun.at(l, pos);
+        // every global operand of the point first (the arrays may alias as far as the compiler knows, so loads
+        // after the first store would wait for it), then the arithmetic, then the stores
+        const int fs[6] = {LOSS_FIELD_S11, LOSS_FIELD_S22, LOSS_FIELD_S12, LOSS_FIELD_S13, LOSS_FIELD_S23,
+                           LOSS_FIELD_S33};
+        T u[6], cu[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          u[f] = a.fld[fs[f]][gi];
+          cu[f] = KAHAN ? a.cmp[fs[f]][gi] : T(0);
+        }
+        const T xa = t[0][gi], xd = t[3][gi], tc = t[2][gi], tb = t[1][gi], te = t[4][gi];
+        const T lam = a.lam ? a.lam[gi] : a.lam0;
+        const T mu = a.mu ? a.mu[gi] : a.mu0;
         const T x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);  // v1 along z
         const T x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);  // v2 along z
         const T x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);  // v3 along z
-        const T xa = t[0][gi], xd = t[3][gi];
-        const T lam = a.lam ? a.lam[gi] : a.lam0;
-        const T mu = a.mu ? a.mu[gi] : a.mu0;
         const T ltr = lam * (xa + xd + x33);
         T s11 = ltr + T(2) * mu * xa, s22 = ltr + T(2) * mu * xd, s33 = ltr + T(2) * mu * x33;
-        T s13 = mu * (t[2][gi] + x13);
+        T s13 = mu * (tc + x13);
         if (a.srcp.on) {
           const int dz = pos - a.srcp.zs + 12, dy = outer - a.srcp.ys + 12, dx = x0 + l - a.srcp.xs + 12;
           if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u) {
@@ -158,13 +171,18 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
             if (a.src_shear) s13 += sv;
           }
         }
-        upd<T, KAHAN>(a.fld[LOSS_FIELD_S11], a.cmp[LOSS_FIELD_S11], gi, s11);
-        upd<T, KAHAN>(a.fld[LOSS_FIELD_S22], a.cmp[LOSS_FIELD_S22], gi, s22);
-        upd<T, KAHAN>(a.fld[LOSS_FIELD_S12], a.cmp[LOSS_FIELD_S12], gi, mu * t[1][gi]);
+        const T d[6] = {s11, s22, mu * tb, s13, mu * (te + x23), s33};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) upd_r<T, KAHAN>(u[f], cu[f], d[f]);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          a.fld[fs[f]][gi] = u[f];
+          if (KAHAN) a.cmp[fs[f]][gi] = cu[f];
+        }
         // new stresses needed by the velocity sub-step's z derivatives stay on chip
-        F[0][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S13], a.cmp[LOSS_FIELD_S13], gi, s13);
-        F[1][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S23], a.cmp[LOSS_FIELD_S23], gi, mu * (t[4][gi] + x23));
-        F[2][k] = upd<T, KAHAN>(a.fld[LOSS_FIELD_S33], a.cmp[LOSS_FIELD_S33], gi, s33);
+        F[0][k] = u[3];
+        F[1][k] = u[4];
+        F[2][k] = u[5];
       });
       __syncthreads();
       if (a.do_A)
@@ -181,9 +199,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
   } else if (PASS == EL_AX) {
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
-      t[5][gi] += effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
-      t[6][gi] += effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
-      t[7][gi] += effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+      const T t5 = t[5][gi], t6 = t[6][gi], t7 = t[7][gi];  // loaded before any store (see EL_BZ)
+      const T y0 = effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
+      const T y1 = effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
+      const T y2 = effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+      t[5][gi] = t5 + y0;
+      t[6][gi] = t6 + y1;
+      t[7][gi] = t7 + y2;
     });
   } else if (PASS == EL_AY) {
     const int outer = blockIdx.x / g.nxb;  // z index of the bundle
@@ -197,12 +219,24 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
         if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u)
           force = (T)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
       }
-      upd<T, KAHAN>(a.fld[LOSS_FIELD_V1], a.cmp[LOSS_FIELD_V1], gi,
-                    b * (t[5][gi] + effA(a, 0, gi, pos, a.s3h * O[0][k], ta)));
-      upd<T, KAHAN>(a.fld[LOSS_FIELD_V2], a.cmp[LOSS_FIELD_V2], gi,
-                    b * (t[6][gi] + effA(a, 1, gi, pos, a.s3h * O[1][k], ta)));
-      upd<T, KAHAN>(a.fld[LOSS_FIELD_V3], a.cmp[LOSS_FIELD_V3], gi,
-                    b * (t[7][gi] + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + force));
+      T u[3], cu[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        u[f] = a.fld[LOSS_FIELD_V1 + f][gi];
+        cu[f] = KAHAN ? a.cmp[LOSS_FIELD_V1 + f][gi] : T(0);
+      }
+      const T t5 = t[5][gi], t6 = t[6][gi], t7 = t[7][gi];
+      const T d0 = b * (t5 + effA(a, 0, gi, pos, a.s3h * O[0][k], ta));
+      const T d1 = b * (t6 + effA(a, 1, gi, pos, a.s3h * O[1][k], ta));
+      const T d2 = b * (t7 + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + force);
+      upd_r<T, KAHAN>(u[0], cu[0], d0);
+      upd_r<T, KAHAN>(u[1], cu[1], d1);
+      upd_r<T, KAHAN>(u[2], cu[2], d2);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        a.fld[LOSS_FIELD_V1 + f][gi] = u[f];
+        if (KAHAN) a.cmp[LOSS_FIELD_V1 + f][gi] = cu[f];
+      }
     });
   }
 }
