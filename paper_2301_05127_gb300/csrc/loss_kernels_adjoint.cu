@@ -74,6 +74,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_adj(AdjArgs<T> 
       m = a.memf[gi];
     }
     const T Z = a.sgn * (Q * m + R * gf);
+    // the accumulated gradients and the adjoint memory variable are loaded with the other operands, before any
+    // store (the arrays may alias as far as the compiler knows)
+    const double g1o = a.g1 ? a.g1[gi] : 0.0;
+    const double g2o = a.g2 ? a.g2[gi] : 0.0;
+    const T mbo = lay ? a.memb[gi] : T(0);
     T ssum = T(0);
     if (a.in[0]) ssum += a.in[0][gi];
     if (a.in[1]) ssum += a.in[1][gi];
@@ -97,11 +102,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_adj(AdjArgs<T> 
       Zh = a.sgn * (Qh * m + Rh * gf);
       xhb = a.sgn * (c2 * rv);
     }
-    if (a.g1) a.g1[gi] += (double)Z * (double)ssum;
-    if (a.g2) a.g2[gi] += (double)Z * (double)(a.gw2 * a3) + (double)Zh * (double)rv;
+    if (a.g1) a.g1[gi] = g1o + (double)Z * (double)ssum;
+    if (a.g2) a.g2[gi] = g2o + ((double)Z * (double)(a.gw2 * a3) + (double)Zh * (double)rv);
     T gb;
     if (lay) {
-      const T mb = a.memb[gi];
+      const T mb = mbo;
       a.memb[gi] = E * mb + Q * xb + Qh * xhb;
       gb = P * mb + R * xb + Rh * xhb;
     } else {
