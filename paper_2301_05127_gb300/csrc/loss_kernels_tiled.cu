@@ -37,12 +37,13 @@ struct ZBun {
   int zb;
   __device__ __forceinline__ int at(int l, int pos) const { return (pos - zb) * 32 + l; }
 };
-// r^d for d < kFirPow - 1; the last entry is 0 (the value used for every d >= kFirPow - 1).
+// r^d for d < kFirPow - 1; the last entry is 0 (the value used for every d >= kFirPow - 1).  Strided over the
+// block: the x blocks of rows with at most 255 intervals hold a single warp, fewer threads than entries.
 __device__ __forceinline__ void fill_rpow(float* rpow, float r) {
-  if (threadIdx.x < kFirPow) {
+  for (int i = threadIdx.x; i < kFirPow; i += blockDim.x) {
     float q = 1.0f;
-    for (int d = 0; d < (int)threadIdx.x; ++d) q *= r;
-    rpow[threadIdx.x] = threadIdx.x == kFirPow - 1 ? 0.0f : q;
+    for (int d = 0; d < i; ++d) q *= r;
+    rpow[i] = i == kFirPow - 1 ? 0.0f : q;
   }
 }
 
