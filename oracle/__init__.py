@@ -15,5 +15,7 @@ Modules
 spline   1-D cubic-B-spline collocation, PMBC weights and closures, local solves, derivatives (Sec. 3.1-3.2)
 wave     acoustic and elastic velocity-stress steppers, Ricker source, receivers, energy (Sec. 2, 3.3, 4)
 adjoint  discrete adjoint of the stepper and the misfit gradient with respect to vp, vs, rho
+exact    closed-form solutions of the Gaussian-pulse experiment (Sec. 4.1), in continuous time and for the
+         Strang-split time stepping with exact spatial derivatives
 """
-from . import adjoint, spline, wave  # noqa: F401
+from . import adjoint, exact, spline, wave  # noqa: F401
