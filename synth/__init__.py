@@ -15,6 +15,9 @@ from .workloads import (  # noqa: F401
     acoustic2d_layered,
     elastic3d_homogeneous,
     elastic3d_heterogeneous,
+    elastic3d_double_layer,
+    DOUBLE_LAYER_UPPER,
+    DOUBLE_LAYER_DEEPER,
     batched_shots,
     gaussian_pulse_2d,
     random_field,
