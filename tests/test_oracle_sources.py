@@ -8,14 +8,19 @@
 * Injected pressure: in an acoustic run whose waves have not reached the ends, the sum of sigma h^2 grows by
   exactly what the B sub-steps add, dt amp f_r(t_n + dt / 2), because the LOSS divergence of a velocity field
   that vanishes near the ends sums to zero up to rounding.
+* Elastic sources inject exactly their own components.  Explosive: sigma11, sigma22 and sigma33 each gain
+  sum dt amp f_r(t_n + dt / 2).  Shear: only sigma13 gains it.  Body force along z: the momentum sum of rho v3
+  gains the impulse of the two A halves, (dt / 2) amp (f_r(t_n) + f_r(t_n+1)) per step.  Every other field sum
+  stays zero: no net force from a moment source, and no net stress from a force.
 """
 import dataclasses
 import math
 
 import numpy as np
+import pytest
 
 from oracle.wave import Simulation, Source, ricker
-from synth import acoustic2d_small
+from synth import acoustic2d_small, elastic3d_homogeneous
 
 
 def test_ricker_is_the_normalised_second_derivative_of_a_gaussian():
@@ -63,3 +68,31 @@ def test_injected_pressure_is_conserved_before_the_waves_reach_the_ends():
     total = sim.state["sigma"].sum() * h2
     assert abs(injected) > 1e-4
     assert abs(total - injected) < 1e-9 * abs(injected), (total, injected)
+
+
+@pytest.mark.parametrize("kind", ["explosive", "shear_xz", "force_z"])
+def test_elastic_sources_inject_exactly_their_own_components(kind):
+    w = elastic3d_homogeneous(n=40, p=2, n_nb=8, steps=0, pml_width=0)
+    # 60 Hz: stop at 0.016 s, near the extremum of the running integral; the field reaches about 11 cells from
+    # the centre and the ends are 20 cells away
+    w = dataclasses.replace(w, src_kinds=(kind,), receivers={}, f0=60.0, t0=1.2 / 60.0)
+    sim = Simulation(w)
+    steps, dt = 12, w.dt
+    sim.step(steps, record=False)
+    stress_in = sum(dt * w.amp * ricker((k + 0.5) * dt, w.f0, w.t0) for k in range(steps))
+    impulse = sum(0.5 * dt * w.amp * (ricker(k * dt, w.f0, w.t0) + ricker((k + 1) * dt, w.f0, w.t0))
+                  for k in range(steps))
+    rho = w.model()[2]
+    vol = float(np.prod(w.h))
+    sums = {f: float((a * (rho if f.startswith("v") else 1.0)).sum()) * vol for f, a in sim.state.items()}
+    expect = {f: 0.0 for f in sums}
+    if kind == "explosive":
+        expect.update(s11=stress_in, s22=stress_in, s33=stress_in)
+    elif kind == "shear_xz":
+        expect["s13"] = stress_in
+    else:
+        expect["v3"] = impulse
+    scale = max(abs(v) for v in expect.values())
+    assert scale > 1e-4
+    for f in sums:
+        assert abs(sums[f] - expect[f]) < 1e-8 * scale, (f, sums[f], expect[f])
