@@ -240,20 +240,23 @@ def elastic3d_double_layer(n: int = 128, nz: Optional[int] = None, p: int = 4, p
         f0=f0, t0=1.2 / f0, receivers={"v3": line}, precision=precision, pml_width=pml_width)
 
 
-def gaussian_pulse_2d(n: int, p: int, n_nb: int = 20, dt: float = 1e-4, steps: int = 200):
-    """The paper's 2-D convergence setup (Sec. 4.1): [-5, 5]^2, c = 50 m/s, rho = 1, zero velocity and the
-    initial pressure exp(-5 (x^2 + z^2)); no source.  Returns (workload, initial sigma)."""
-    shape = (n + 1, n + 1)
+def gaussian_pulse_2d(n: int, p: int, n_nb: int = 20, dt: float = 1e-4, steps: int = 200, pad: int = 0):
+    """The paper's 2-D convergence setup (Sec. 4.1): [-5, 5]^2 with n intervals per axis, c = 50 m/s, rho = 1,
+    zero velocity and the initial pressure exp(-5 (x^2 + z^2)); no source.  ``pad`` adds that many points of the
+    same spacing beyond [-5, 5] on every side, room for an absorbing layer outside the domain (p patches then
+    cut n + 2 pad intervals).  Returns (workload, initial sigma)."""
+    nt = n + 2 * pad
+    shape = (nt + 1, nt + 1)
     h = 10.0 / n
-    x = -5.0 + h * np.arange(n + 1)
+    x = -5.0 + h * (np.arange(nt + 1) - pad)
     sigma0 = np.exp(-5.0 * (x[:, None] ** 2 + x[None, :] ** 2))
 
     def model():
         return np.full(shape, 50.0), None, np.full(shape, 1.0)
 
-    w = Workload(name=f"gauss2d_{n}_p{p}", dim=2, physics="acoustic", n=(n, n), p=(p, p), h=(h, h),
-                 n_nb=n_nb, dt=dt, steps=steps, model_fn=model, src_index=(n // 2, n // 2), src_kinds=(),
-                 f0=1.0, t0=0.0, amp=0.0, precision="fp64")
+    w = Workload(name=f"gauss2d_{n}_p{p}" + (f"_pad{pad}" if pad else ""), dim=2, physics="acoustic", n=(nt, nt),
+                 p=(p, p), h=(h, h), n_nb=n_nb, dt=dt, steps=steps, model_fn=model, src_index=(nt // 2, nt // 2),
+                 src_kinds=(), f0=1.0, t0=0.0, amp=0.0, precision="fp64")
     return w, sigma0
 
 
