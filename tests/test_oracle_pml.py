@@ -6,6 +6,7 @@ import numpy as np
 from oracle.exact import pulse_on_grid
 from oracle.wave import PML, Simulation
 from synth import acoustic2d_small, gaussian_pulse_2d
+from synth.workloads import Workload
 
 
 def test_exponential_flow_is_exact_for_frozen_gradient():
@@ -131,3 +132,26 @@ def test_layer_absorbs_the_gaussian_pulse_over_the_papers_time_range():
     assert abs(errs[pad, 1000] / errs[0, 1000] - 1.0) < 1e-3, errs
     assert errs[pad, 2000] < 1.2 * errs[pad, 1000], errs
     assert errs[0, 2000] > 1.0, errs
+
+
+def _normal_incidence_reflection(L, R, n=400, h=10.0, c=2000.0, rho=1000.0, width=6.0):
+    """Largest |v3| left in the interior after a plane packet (6-cell Gaussian, sigma = rho c v3 so that it moves to
+    +z) has entered an L-point layer at the z end and had time to come back to its start."""
+    shape = (n + 1, 5)
+    w = Workload(name="pml_column", dim=2, physics="acoustic", n=(n, 4), p=(1, 1), h=(h, h), n_nb=20,
+                 dt=0.4 * h / c, steps=0, model_fn=lambda: (np.full(shape, c), None, np.full(shape, rho)),
+                 src_index=(0, 0), src_kinds=(), f0=1.0, t0=0.0, amp=0.0, precision="fp64", pml_width=L, pml_R=R)
+    z = np.arange(n + 1)
+    g = np.exp(-(((z - n // 2) / width) ** 2))[:, None] * np.ones(shape)
+    sim = Simulation(w, state={"sigma": rho * c * g, "v1": 0 * g, "v3": g.copy()})
+    sim.step(int(round(2 * (n - n // 2) * h / c / w.dt)), record=False)
+    return float(np.abs(sim.state["v3"][L:n + 1 - L, 2]).max())
+
+
+def test_layer_meets_its_design_reflection_at_normal_incidence():
+    """d0 = -3 c log(R) / (2 L) makes the round trip through a continuous layer attenuate by exactly R (Sec. 3.3).
+    The discrete layer of 50 points returns 1.7e-6 of a unit packet for R = 1e-6 and 1.6e-7 for R = 1e-9.  A
+    20-point layer adds discretisation reflection (1.2e-5 for R = 1e-6)."""
+    assert _normal_incidence_reflection(50, 1e-6) < 3e-6
+    assert _normal_incidence_reflection(50, 1e-9) < 3e-7
+    assert _normal_incidence_reflection(20, 1e-6) > 5e-6
