@@ -1,5 +1,6 @@
 """Writes tests/golden/pml_tables_oracle.txt: the FP64 oracle's errors for the paper's ADE-PML study (Sec. 4.1,
-Tables PML_error_L_t020, err_PML_R and err_PML_kmax) on 512^2 intervals.
+Tables PML_error_L_t020, err_PML_R and err_PML_kmax) on 512^2 intervals, and for the rows of Table 2d_error
+after the wave has left the domain (t >= 0.1 s) on 64^2 .. 256^2 intervals with the layer of the 512^2 runs.
 
 The Gaussian pulse of Sec. 4.1 runs on [-5, 5]^2 padded by L points on every side, with the absorbing layer in the
 padding: thickness L points, reflection coefficient R, cut-off k_max, and f_P = c_P / L with L in points as
@@ -19,11 +20,12 @@ import multiprocessing as mp
 import os
 import sys
 
-# (L, R, k_max): the thickness study at R = 1e-6, k_max = 1; the R study at L = 50; the k_max study at L = 50
-CONFIGS = [(10, 1e-6, 1.0), (20, 1e-6, 1.0), (50, 1e-6, 1.0),
-           (50, 1e-1, 1.0), (50, 1e-3, 1.0), (50, 1e-9, 1.0),
-           (50, 1e-6, 0.5), (50, 1e-6, 6.0)]
-N = 512
+# (N, L, R, k_max): on 512^2 the thickness study at R = 1e-6, k_max = 1, the R study at L = 50 and the k_max
+# study at L = 50; on 64^2 .. 256^2 the convergence rows with L = 50 and R = 1e-6 or 1e-9
+CONFIGS = [(512, 10, 1e-6, 1.0), (512, 20, 1e-6, 1.0), (512, 50, 1e-6, 1.0),
+           (512, 50, 1e-1, 1.0), (512, 50, 1e-3, 1.0), (512, 50, 1e-9, 1.0),
+           (512, 50, 1e-6, 0.5), (512, 50, 1e-6, 6.0)] + \
+          [(n, 50, R, 1.0) for n in (64, 128, 256) for R in (1e-6, 1e-9)]
 TIMES = tuple(range(600, 2001, 200))  # steps of 1e-4 s: 0.06 .. 0.20 s
 
 
@@ -37,8 +39,8 @@ def run(cfg):
     from oracle.wave import Simulation
     from synth import gaussian_pulse_2d
 
-    L, R, kmax = cfg
-    w, s0 = gaussian_pulse_2d(N, p=4, n_nb=20, dt=1e-4, steps=TIMES[-1], pad=L)
+    N, L, R, kmax = cfg
+    w, s0 = gaussian_pulse_2d(N, p=2, n_nb=20, dt=1e-4, steps=TIMES[-1], pad=L)
     w = dataclasses.replace(w, pml_width=L, pml_R=R, pml_kmax=kmax, f0=50.0 / L)
     sim = Simulation(w, state={"sigma": s0, "v1": 0 * s0, "v3": 0 * s0})
     out, done = [], 0
@@ -53,16 +55,17 @@ def run(cfg):
 
 def main():
     ctx = mp.get_context("spawn")
-    with ctx.Pool(min(len(CONFIGS), os.cpu_count() or 1)) as pool:
+    with ctx.Pool(min(len(CONFIGS), os.cpu_count() or 1)) as pool:  # the 512^2 runs first: they take longest
         results = pool.map(run, CONFIGS)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pml_tables_oracle.txt")
     with open(path, "w") as f:
-        f.write("# FP64 oracle, Gaussian pulse of Sec. 4.1 on 512^2 intervals padded by L points with the layer in the\n")
-        f.write("# padding (Tables PML_error_L_t020, err_PML_R, err_PML_kmax); written by tests/golden/make_pml_tables.py.\n")
-        f.write("# columns: L  R  k_max  steps  rel_l2(v3)  eps2(v3) = ||e||_2 / max|v3_ref|\n")
-        for (L, R, kmax), rows in results:
+        f.write("# FP64 oracle, Gaussian pulse of Sec. 4.1 on N^2 intervals padded by L points with the layer in the\n")
+        f.write("# padding (Tables PML_error_L_t020, err_PML_R, err_PML_kmax, 2d_error); written by\n")
+        f.write("# tests/golden/make_pml_tables.py.\n")
+        f.write("# columns: N  L  R  k_max  steps  rel_l2(v3)  eps2(v3) = ||e||_2 / max|v3_ref|\n")
+        for (N, L, R, kmax), rows in results:
             for steps, rel, eps2 in rows:
-                f.write(f"{L} {R:.0e} {kmax} {steps} {rel:.6e} {eps2:.6e}\n")
+                f.write(f"{N} {L} {R:.0e} {kmax} {steps} {rel:.6e} {eps2:.6e}\n")
     print("wrote", path)
 
 
