@@ -155,3 +155,34 @@ def test_layer_meets_its_design_reflection_at_normal_incidence():
     assert _normal_incidence_reflection(50, 1e-6) < 3e-6
     assert _normal_incidence_reflection(50, 1e-9) < 3e-7
     assert _normal_incidence_reflection(20, 1e-6) > 5e-6
+
+
+def test_pml_study_reproduces_the_papers_findings():
+    """The oracle's ADE-PML study on 512^2 (tests/golden/pml_tables_oracle.txt, written by make_pml_tables.py from
+    oracle/ only) shows what Sec. 4.1 reports: every layer gives the same error until the wave reaches it; at
+    0.2 s the error falls with the thickness L and the reflection coefficient R; k_max = 1 is the best cut-off;
+    and up to 0.10 s the error falls by 2^4 per doubling of N (Table 2d_error).  Errors are eps_2 = h ||e|| / A
+    (one amplitude for the run)."""
+    import collections
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "pml_tables_oracle.txt")
+    e = collections.defaultdict(dict)
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        N, L, R, k, steps, _, _, eps2a = line.split()
+        e[int(N), int(L), float(R), float(k)][int(steps)] = float(eps2a)
+    study = [c for c in e if c[0] == 512]
+    for steps in (200, 400, 600):
+        vals = [e[c][steps] for c in study]
+        assert max(vals) < 1.01 * min(vals), steps
+    t = 2000
+    assert e[512, 10, 1e-6, 1.0][t] > e[512, 20, 1e-6, 1.0][t] > e[512, 50, 1e-6, 1.0][t]
+    assert e[512, 50, 1e-1, 1.0][t] > e[512, 50, 1e-3, 1.0][t] > e[512, 50, 1e-6, 1.0][t] > e[512, 50, 1e-9, 1.0][t]
+    late = lambda c: max(e[c][s] for s in range(1000, 2001, 200))
+    assert late((512, 50, 1e-6, 1.0)) < 0.2 * min(late((512, 50, 1e-6, 0.5)), late((512, 50, 1e-6, 6.0)))
+    for steps in (200, 400, 600, 1000):
+        for n in (64, 128, 256):
+            order = np.log2(e[n, 50, 1e-6, 1.0][steps] / e[2 * n, 50, 1e-6, 1.0][steps])
+            assert 3.9 < order < 4.4, (n, steps, order)
