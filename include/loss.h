@@ -133,7 +133,8 @@ loss_status_t loss_set_source(loss_handle_t handle, int32_t shot, const int64_t 
  * d0 = -3 c_max log(R) / (2 width h), c_max = max vp of the model (so loss_set_model must come first, else
  * LOSS_E_STATE).  Memory variables start at zero.  Each sub-step integrates the memory variables exactly
  * with the other subsystem frozen (the exponential operator splitting of Sec. 3.3).
- * LOSS_E_ARG unless 2 * width <= n on every axis, 0 < R < 1, k_max >= 1 and f0 > 0. */
+ * LOSS_E_ARG unless 2 * width <= n on every axis, 0 < R < 1, k_max > 0 and f0 > 0 (the study of Sec. 4.1
+ * takes k_max from 0.5 to 19; k_max = 1 absorbs best). */
 loss_status_t loss_set_pml(loss_handle_t handle, int32_t shot, int32_t width, double R, double k_max, double f0);
 
 /* Record field `field` of shot `shot` at the n dense flat indices flat_idx (int64, copied) after every

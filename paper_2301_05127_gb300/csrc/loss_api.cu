@@ -872,7 +872,7 @@ static loss_status_t rebuild_receivers(loss_ctx* h, Shot& s) {
 loss_status_t loss_set_pml(loss_handle_t h, int32_t shot, int32_t width, double R, double k_max, double f0) {
   Shot* s;
   LOSS_TRY(get_shot(h, shot, &s));
-  if (width < 0 || !(R > 0.0 && R < 1.0) || !(k_max >= 1.0) || !(f0 > 0.0))
+  if (width < 0 || !(R > 0.0 && R < 1.0) || !(k_max > 0.0) || !(f0 > 0.0))
     return fail(h, LOSS_E_ARG, "bad PML parameters");
   for (int k = 0; k < 3; ++k)
     if (!(s->dim == 2 && k == 1) && 2 * (int64_t)width > s->n[k]) return fail(h, LOSS_E_ARG, "PML wider than half an axis");
