@@ -2,8 +2,8 @@
 
 Argument marshalling only: every step of the method runs in the CUDA kernels behind include/loss.h.  The
 functions of the C ABI are exposed under their C names (``loss_create_grid``, ``loss_step`` ...) through
-``lib()``; the ``Grid`` class wraps a handle with numpy / torch conveniences.  Importing this package fails
-loudly when the shared library has not been built (``python -m paper_2301_05127_gb300.build`` or
+``lib()``; the ``Grid`` class wraps a handle with numpy / torch conveniences.  The first call into the library
+raises ImportError when the shared library has not been built (``python -m paper_2301_05127_gb300.build`` or
 ``__graft_entry__.build()``): there is no fallback implementation.
 """
 from __future__ import annotations
@@ -120,11 +120,13 @@ def _check(st, handle=None):
 def _ptr_and_mem(a):
     """(pointer, mem) of a numpy array or a torch tensor."""
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"]
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libloss must be C-contiguous")
         return a.ctypes.data, LOSS_MEM_HOST
     import torch
     if isinstance(a, torch.Tensor):
-        assert a.is_contiguous()
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to libloss must be contiguous")
         return a.data_ptr(), (LOSS_MEM_DEVICE if a.is_cuda else LOSS_MEM_HOST)
     raise TypeError(type(a))
 
