@@ -10,7 +10,8 @@ is the time derivative of Stokes' displacement solution:
 
 with F = amp f_r, the Ricker wavelet, whose antiderivative is (t - t0) exp(-(pi f0 (t - t0))^2).  Receivers sit
 12 cells from the source along the force, across it, on a diagonal and off every axis, on a 49^3 grid with a
-10-point absorbing layer.  The difference is the discretisation error, 0.2-0.25 % of the peak.  A wrong modulus, buoyancy, force timing or sign would show as several percent or more.
+10-point absorbing layer.  The difference is the discretisation error, 0.2-0.25 % of the peak.  A wrong modulus,
+buoyancy, force timing or sign would show as several percent or more.
 """
 import dataclasses
 import math
