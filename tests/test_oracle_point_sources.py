@@ -1,6 +1,6 @@
 """Pins of the oracle's 3-D elastic source-to-receiver path (CPU only) against exact solutions in a homogeneous
-medium, summed over the source's Gaussian profile: a body force along z against Stokes' point-force solution, and
-the explosive source against the pure P field it must radiate.
+medium, summed over the source's Gaussian profile: a body force along z against Stokes' point-force solution, the
+explosive source against the pure P field it must radiate, and the shear source against its double couple.
 
 For a force F(t) along x_j at the origin (rho, P speed alpha, S speed beta, gamma = x / r), the particle velocity
 is the time derivative of Stokes' displacement solution:
@@ -18,6 +18,12 @@ The explosive source adds s(t) A(x) to the rate of each normal stress (s = amp f
 s, that is the body force S(t) grad A.  Its field is the gradient of a P potential phi with phi_tt - alpha^2
 Laplacian phi = S A / rho, so v = grad sum_k A_k h^3 s(t - r_k / alpha) / (4 pi rho alpha^2 r_k): radial, with no S
 wave.  It agrees to 0.22-0.26 % of the peak, and the components an S wave would carry stay at rounding level.
+
+The shear source adds s A to the rate of sigma13 (x-z).  That is the body force S (d_z A, 0, d_x A), a double
+couple, whose velocity is sum_k A_k h^3 (d_z U^(x) + d_x U^(z)), where U^(j) is Stokes' displacement for a force of
+history s along x_j.  The tau-weighted integral in U uses the closed form of int s f_r(s) ds.  The spatial
+derivatives are central differences of the closed form with a 1 cm step, against a 55 m time scale.  It agrees
+to 0.08-0.31 % of the peak.
 """
 import dataclasses
 import math
@@ -59,6 +65,44 @@ def _stokes_velocity(dx, weight, t, alpha, beta, rho, f0, t0, amp, j):
         far = gij / (alpha**2 * r) * _ricker_rate(ta, f0, t0) - (gij - dij) / (beta**2 * r) * _ricker_rate(tb, f0, t0)
         out[i] = amp / (4.0 * math.pi * rho) * float(np.sum(weight * (near + far)))
     return out
+
+
+def _ricker_moment(t, f0, t0):
+    """An antiderivative of s f_r(s): exp(-c x^2) (x^2 + 1 / (2c)) + t0 x exp(-c x^2), x = s - t0, c = (pi f0)^2."""
+    x = t - t0
+    c = (math.pi * f0) ** 2
+    return np.exp(-c * x * x) * (x * x + 0.5 / c) + t0 * x * np.exp(-c * x * x)
+
+
+def _stokes_displacement(dx, t, alpha, beta, rho, f0, t0, amp, j):
+    """Displacement [points, 3] (array-axis order) of a force amp f_r along array axis j at each offset -dx."""
+    r = np.linalg.norm(dx, axis=1)
+    g = dx / r[:, None]
+    ta, tb = t - r / alpha, t - r / beta
+    # int_{r / alpha}^{r / beta} tau F(t - tau) dtau = int_{tb}^{ta} (t - s) F(s) ds
+    J = t * (_ricker_integral(ta, f0, t0) - _ricker_integral(tb, f0, t0)) - (_ricker_moment(ta, f0, t0)
+                                                                             - _ricker_moment(tb, f0, t0))
+    out = np.empty((len(r), 3))
+    for i in range(3):
+        gij = g[:, i] * g[:, j]
+        dij = 1.0 if i == j else 0.0
+        out[:, i] = amp / (4.0 * math.pi * rho) * ((3.0 * gij - dij) / r**3 * J + gij / (alpha**2 * r) * _ricker(ta, f0, t0)
+                                                   - (gij - dij) / (beta**2 * r) * _ricker(tb, f0, t0))
+    return out
+
+
+def _shear_velocity(dx, weight, t, alpha, beta, rho, f0, t0, amp, step=1e-2):
+    """Velocity of the weighted x-z double couples: sum of d_z U^(x) + d_x U^(z) (array axes: x = 2, z = 0)."""
+    keep = np.linalg.norm(dx, axis=1) > 1.0
+    dx, weight = dx[keep], weight[keep]
+    total = np.zeros(3)
+    for n, m in ((2, 0), (0, 2)):
+        e = np.zeros(3)
+        e[m] = step
+        du = (_stokes_displacement(dx + e, t, alpha, beta, rho, f0, t0, amp, n)
+              - _stokes_displacement(dx - e, t, alpha, beta, rho, f0, t0, amp, n)) / (2.0 * step)
+        total += (weight[:, None] * du).sum(0)
+    return total
 
 
 def _explosion_velocity(dx, weight, t, alpha, rho, f0, t0, amp):
@@ -113,5 +157,15 @@ def test_explosive_source_radiates_the_exact_p_field():
     for r in RECEIVERS:
         dx = (np.array(r)[None, :] - O) * w.h[0]
         exact = np.array([_explosion_velocity(dx, A, t, vp, rho, w.f0, w.t0, w.amp) for t in times])
+        err = np.abs(np.array(traces[r]) - exact).max() / np.abs(exact).max()
+        assert err < 1e-2, (r, err)
+
+
+def test_shear_source_radiates_the_exact_double_couple_field():
+    w, O, A, times, traces = _run("shear_xz", 0.24)
+    vp, vs, rho = (float(a.flat[0]) for a in w.model())
+    for r in RECEIVERS:
+        dx = (np.array(r)[None, :] - O) * w.h[0]
+        exact = np.array([_shear_velocity(dx, A, t, vp, vs, rho, w.f0, w.t0, w.amp) for t in times])
         err = np.abs(np.array(traces[r]) - exact).max() / np.abs(exact).max()
         assert err < 1e-2, (r, err)
