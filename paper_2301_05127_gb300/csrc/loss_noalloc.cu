@@ -1,12 +1,12 @@
 // loss_derivative_noalloc: the stand-alone LOSS derivative for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at all: code that runs inside another framework's memory pool or
-// allocator hooks, inside a captured or replayed stream where an allocation would break the capture, or under a
-// memory budget that forbids new allocations after start-up.  loss_create_grid allocates (fields, tables), so
-// such callers cannot use a handle.  This entry point needs no handle: the caller passes device input and output
-// arrays, and the only device memory the kernel reads besides them -- the PMBC weights of the axis and the
-// Thomas factors -- lives in the file-scope static array below, which every GPU that loads this library holds
-// until the process exits.
+// allocator hooks, which owns every device allocation of the process, or under a memory budget that forbids new
+// allocations after start-up.  loss_create_grid allocates (fields, tables), so such callers cannot use a handle.
+// This entry point needs no handle: the caller passes device input and output arrays, and the only device memory
+// the kernel reads besides them -- the PMBC weights of the axis and the Thomas factors -- lives in the file-scope
+// static array below, which every GPU that loads this library holds until the process exits.  Each device has its
+// own copy of the array; calls on one device whose work overlaps on the GPU race on that copy.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -86,8 +86,12 @@ using namespace lossk;
 extern "C" loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis, const void* f, void* d1,
                                                  void* cuda_stream) {
   if (!desc || !f || !d1) return LOSS_E_ARG;
+  // Only the geometry matters here: physics and dt take neutral values, so a caller may leave them unset.
+  loss_grid_desc_t geo = *desc;
+  geo.physics = LOSS_ACOUSTIC;
+  geo.dt = 1.0;
   std::string why;
-  loss_status_t st = validate(*desc, &why);
+  loss_status_t st = validate(geo, &why);
   if (st != LOSS_OK) return st;
   if (axis < 0 || axis >= desc->dim) return LOSS_E_ARG;
   int dev = 0, smem = 0;
@@ -100,7 +104,7 @@ extern "C" loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, i
   ctx.device = dev;
   ctx.smem_optin = smem;
   Shot s;
-  s.d = *desc;
+  s.d = geo;
   shot_geometry(s);
   const int k = (s.dim == 3) ? axis : (axis == 0 ? 0 : 2);
   if (s.esize == 8)

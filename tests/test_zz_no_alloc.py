@@ -1,7 +1,8 @@
 """loss_derivative_noalloc, the derivative entry point for callers that cannot allocate device memory (for
-example code running under another framework's allocator or inside a stream capture).  It keeps its tables in a
-static device array instead of handle-owned memory; its output must equal the handle-based loss_derivative's,
-also when two calls with different grids come one after the other (the second rewrites the shared tables)."""
+example code running under another framework's allocator, which owns every device allocation).  It keeps its
+tables in a static device array instead of handle-owned memory.  Both paths launch the same kernel with the same
+tables, so its output must equal the handle-based loss_derivative's bit for bit, also when two calls with
+different grids come one after the other (the second rewrites the shared tables)."""
 import ctypes
 
 import numpy as np
@@ -14,7 +15,6 @@ CASES = [
     (2, (64, 96), (2, 3), 12, (1.0, 0.5), "fp32", 1),
     (3, (24, 32, 40), (2, 2, 4), 10, (1.0, 1.5, 0.5), "fp64", 0),
 ]
-TOL = {"fp64": 1e-12, "fp32": 2e-5}
 
 
 def test_noalloc_matches_handle_derivative_on_two_calls_in_a_row():
@@ -40,12 +40,13 @@ def test_noalloc_matches_handle_derivative_on_two_calls_in_a_row():
         descs.append(d)
     torch.cuda.synchronize()
     for d, (ft, out, axis, _) in zip(descs, outs):  # two calls in a row, different grids and precisions
+        d.dt = 0.0  # only the geometry is read: an unset time step is accepted
         st = L.loss_derivative_noalloc(ctypes.byref(d), axis, ft.data_ptr(), out.data_ptr(), stream)
         assert st == pkg.LOSS_OK, L.loss_status_str(st)
     torch.cuda.synchronize()
     for ref, (_, out, _, prec) in zip(refs, outs):
         got = out.cpu().numpy()
-        assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
+        assert np.array_equal(got, ref), prec
 
 
 def test_noalloc_rejects_tables_beyond_the_static_array():
