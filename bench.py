@@ -185,6 +185,13 @@ def _timed_steps(torch, g, steps, flush):
 
 KERNELS = ("acoustic_x", "acoustic_z", "acoustic_z2")
 
+# Algorithmic bytes per point-step of one whole step (FP32): every state array and the model read once and every
+# state array written once.  2-D acoustic: sigma, v1, v3 read and written, kappa read (the benchmark's density
+# is constant, so the buoyancy is a scalar): 7 x 4 = 28 B; the FP32 compensation arrays of the three fields
+# add 3 x 2 x 4 = 24 B.  3-D elastic, constant model: nine fields read and written, 18 x 4 = 72 B.
+STEP_ALG_BYTES, STEP_COMP_BYTES = 28, 24
+ELASTIC_ALG_BYTES = 72
+
 
 def _alg_bytes_per_point(kernel, esize, kahan, b_array):
     """Algorithmic DRAM bytes per grid point of one launch of the FP32 step's kernels: every array the kernel must
@@ -231,15 +238,18 @@ def _batched_leg(torch, pkg, units, warmup_units, k):
     conv = g.profile_read("acoustic_z2")[1] > 0  # the convolution kernels split z into Z1 and Z2
     g.close()
     peak, kind = _peaks()
-    # B per point-step: x kernel 24 (v1, sigma, kappa, d_z v3 read; sigma, v1 written); z: line kernel 16 (sigma, v3
-    # read; v3, d_z v3 written), or Z1 12 (sigma, v3 read; v3 written) + Z2 8 (v3 read; d_z v3 written)
-    alg = 44 if conv else 40
+    # Algorithmic bytes per point-step: the step's 28 B (sigma, v1, v3 read and written, kappa read).  The kernels
+    # themselves touch 44 B (convolution: x 24, Z1 12, Z2 8, with the d_z v3 temporary) or 40 B (line kernels).
+    alg = STEP_ALG_BYTES
+    own = 44 if conv else 40
     value = pts / (ms * 1e-3)
     return {"workload": f"{len(ws)} shots, n from {min(w.n[0] for w in ws)} to {max(w.n[0] for w in ws)}, M=128, "
                         f"n_nb=20, PML 40, FP32, graph of {k} steps",
             "kernels": "truncated-convolution" if conv else "line",
             "points_per_step": pts, "value": value, "unit": UNIT, "ms_per_step": ms,
-            "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9), "peak_kind": peak_kind_note(kind),
+            "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9),
+            "kernel_bytes_per_point": own, "kernel_bytes_frac_of_peak": value * own / (peak * 1e9),
+            "peak_kind": peak_kind_note(kind),
             "autotune": tune, "launches": launches, "l2": "working set 4.5 GB, no flush"}
 
 
@@ -261,14 +271,17 @@ def _elastic_leg(torch, pkg, steps, warmup, flush):
     g.close()
     ms_step = sum(ms) / len(ms)
     peak, kind = _peaks()
-    # B per point-step of the five passes with a constant model (FP32, compensated stress and velocity
-    # updates): BX 24, BY 28, BZ 140, AX 36, AY 72 (every array a pass must touch, once)
-    alg = 300
+    # Algorithmic bytes per point-step of the elastic step with a constant model: the nine FP32 fields read and
+    # written once, 72 B; the compensation arrays of the nine fields add another 72 B (read and written once).
+    # Derivative temporaries are not algorithmic.
+    alg, alg_comp = ELASTIC_ALG_BYTES, 2 * ELASTIC_ALG_BYTES
     value = w.points / (ms_step * 1e-3)
     return {"workload": "elastic3d_homogeneous 257^3 pts, 4x4x4 patches (M=64), n_nb=20, PML 20, FP32 + Kahan",
             "value": value, "unit": UNIT, "ms_per_step": ms_step,
             "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items()},
             "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9),
+            "alg_bytes_per_point_with_compensation": alg_comp,
+            "alg_frac_of_peak_with_compensation": value * alg_comp / (peak * 1e9),
             "peak_kind": peak_kind_note(kind), "l2": "flushed between timed steps", "autotune": tune}
 
 
@@ -292,6 +305,45 @@ def _adjoint_leg(steps):
                         f"checkpoints every {int(math.ceil(math.sqrt(steps)))} steps",
             "ms_per_step": 1e3 * wall / steps, "value": w.points * steps / wall, "unit": UNIT + " (forward+adjoint)",
             "misfit": J}
+
+
+def _accuracy_leg(pkg):
+    """The benchmark workload over its whole length (2000 steps) in the headline precision (FP32 + compensation,
+    the timed kernels) and in FP64, compared with the FP64 oracle's golden run of the same workload
+    (tests/golden/full_acoustic2d_layered.npz, written by tests/golden/make_full_runs.py from the oracle):
+    pressure traces after every step on lines through the source, and every field at four checkpoints on a
+    sub-grid of stride 16.  Errors: max |gpu - ref| / max |ref| (traces) and ||gpu - ref||_2 over the largest
+    ||ref||_2 of the run (fields)."""
+    import importlib.util
+
+    path = os.path.join(ROOT, "tests", "golden", "make_full_runs.py")
+    spec = importlib.util.spec_from_file_location("make_full_runs", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    name = "acoustic2d_layered"
+    if not os.path.exists(mod.path_of(name)):
+        return {"unavailable": f"golden run {os.path.relpath(mod.path_of(name), ROOT)} missing"}
+    gold = dict(np.load(mod.path_of(name)))
+    w, stride = mod.golden_workload(name)
+    sl = tuple(slice(None, None, stride) for _ in range(w.dim))
+    res = {"reference": "FP64 oracle, golden run tests/golden/full_acoustic2d_layered.npz", "steps": w.steps}
+    for prec in ("fp32_kahan", "fp64"):
+        g = pkg.Grid.from_workloads([w], precision=prec)
+        done, worst, peak = 0, {}, {}
+        for i, c in enumerate(gold["ckpt_steps"]):
+            g.step(int(c) - done)
+            done = int(c)
+            for f in ("sigma", "v1", "v3"):
+                ref = gold[f"snap_{f}"][i]
+                got = g.get_field(0, f).astype(np.float64)[sl]
+                worst[f] = max(worst.get(f, 0.0), float(np.linalg.norm(got - ref)))
+                peak[f] = max(peak.get(f, 0.0), float(np.linalg.norm(ref)))
+        tr = g.record(0)["sigma"].astype(np.float64)
+        g.close()
+        ref_tr = gold["trace_sigma"]
+        res[prec] = {"trace_rel_max": float(np.abs(tr - ref_tr).max() / np.abs(ref_tr).max()),
+                     "field_rel_l2_max": max(worst[f] / peak[f] for f in worst)}
+    return res
 
 
 def peak_kind_note(kind):
@@ -349,17 +401,15 @@ def run_ours(args):
     ms_per_step = sum_ms / args.steps
     value = job_value(ws, pts, ms_per_step)
 
-    # dominant kernel roofline
+    # dominant kernel roofline: the step's algorithmic bytes (28 B per point) over one launch of the dominant
+    # kernel, which processes every point of the grid once per step
     dom = max(KERNELS, key=lambda k: kern[k][0])
     dom_ms = kern[dom][0] / max(kern[dom][1], 1)
-    alg = _alg_bytes_per_point(dom, 4, True, False) * pts
+    alg = STEP_ALG_BYTES * pts
     peak, peak_kind = _peaks()
     achieved = alg / (dom_ms * 1e-3) / 1e9
     traffic = _traffic(dom)
-
-    # accuracy of the timed FP32 run against the FP64 form of the same run (the FP64 form matches the FP64
-    # oracle in the parity tests)
-    s32 = g.get_field(0, "sigma").astype(np.float64)
+    own = _alg_bytes_per_point(dom, 4, True, False) * pts  # every array the kernel itself reads or writes, once
 
     # --- FP64 form ---------------------------------------------------------------------------------------
     g64 = pkg.Grid.from_workloads([w], precision="fp64")
@@ -368,13 +418,11 @@ def run_ours(args):
     n64 = max(1, min(args.steps, max(3, args.steps // 2)))
     ms64 = _timed_steps(torch, g64, n64, flush)
     fp64_ms = slowest(sum(ms64)) / len(ms64)
-    # same number of steps as the FP32 run (timed and profiled passes) for the accuracy comparison
-    if 2 * args.steps > len(ms64):
-        g64.step(2 * args.steps - len(ms64))
-    s64 = g64.get_field(0, "sigma")
-    rel_fp32 = float(np.linalg.norm(s32 - s64) / max(np.linalg.norm(s64), 1e-300))
     g64.close()
     g.close()
+
+    # --- accuracy over the whole run against the FP64 oracle's golden run -------------------------------------
+    accuracy = _accuracy_leg(pkg) if not args.no_accuracy else None
 
     # --- batched multi-shot survey, 3-D elastic step, misfit gradient ---------------------------------------
     batched = _batched_leg(torch, pkg, units=3, warmup_units=1, k=10) if not args.no_batched else None
@@ -419,14 +467,19 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write + read)", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "alg_bytes_per_launch": alg, "avg_launch_ms": dom_ms,
+                         "alg_bytes_per_point": STEP_ALG_BYTES, "alg_bytes_per_launch": alg, "avg_launch_ms": dom_ms,
+                         "traffic_over_alg": None if traffic is None else traffic / alg,
+                         "kernel_own_bytes_per_launch": own, "kernel_own_frac": own / (dom_ms * 1e-3) / 1e9 / peak,
+                         "step_frac": STEP_ALG_BYTES * pts / (ms_per_step * 1e-3) / 1e9 / peak,
+                         "step_frac_with_compensation": (STEP_ALG_BYTES + STEP_COMP_BYTES) * pts
+                         / (ms_per_step * 1e-3) / 1e9 / peak,
                          "durations": "CUDA events around each launch in a second pass of K flushed steps"},
             "ms_per_step_with_launch_events": sum(prof_ms) / len(prof_ms),
             "kernels_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in kern.items()},
             "kernels_frac_of_peak": {k: _alg_bytes_per_point(k, 4, True, False) * pts / (kern[k][0] / kern[k][1] * 1e-3)
                                      / (peak * 1e9) for k in KERNELS if kern[k][1]},
             "fp64": {"value": job_value(ws, pts, fp64_ms), "ms_per_step": fp64_ms, "unit": UNIT},
-            "accuracy": {"rel_l2_fp32kahan_vs_fp64_after_run": rel_fp32, "steps": args.warmup + 2 * args.steps},
+            "accuracy": accuracy,
             "e2e": {"value": ws * pts * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps, "ms_total": e2e_ms, "runs_ms": e2e_runs},
             "batched": batched,
@@ -444,37 +497,43 @@ def run_ours(args):
 
 
 def _oracle_steps(steps, warmup):
-    """Time the FP64 oracle on the benchmark workload: each step a full Strang step of the full grid."""
-    from oracle.wave import Simulation
+    """Time the FP64 oracle on the benchmark workload: each step a full Strang step of the full grid.  The oracle
+    runs as it stands, with the derivative terms of each sub-step spread over one worker process per host core
+    but one (oracle.parallel, equal to the serial oracle bit for bit).  Returns (pt-upd/s, cores used, wall s,
+    workers): cores = CPU seconds of the parent and the workers over the timed steps / their wall time."""
+    from oracle.parallel import ParallelSimulation
     from synth import acoustic2d_layered
 
     w = acoustic2d_layered(precision="fp64")
-    sim = Simulation(w)
-    sim.step(warmup, record=False)
-    c0, t0 = time.process_time(), time.perf_counter()
-    sim.step(steps, record=False)
-    wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    return w.points * steps / wall, max(1, round(cpu / wall)), wall
+    workers = max(1, (os.cpu_count() or 2) - 1)
+    with ParallelSimulation(w, workers=workers) as sim:
+        sim.step(max(1, warmup), record=False)
+        c0, t0 = sim.cpu_time(), time.perf_counter()
+        sim.step(steps, record=False)
+        wall = time.perf_counter() - t0
+        cpu = sim.cpu_time() - c0
+    return w.points * steps / wall, max(1, round(cpu / wall)), wall, workers
 
 
 def cpu_baseline():
-    v, cores, wall = _oracle_steps(steps=2, warmup=0)
+    v, cores, wall, workers = _oracle_steps(steps=20, warmup=1)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"2 full Strang steps of the 2049^2 FP64 oracle ({wall:.1f} s); host {os.cpu_count()} cores"}
+            "sample": f"20 full Strang steps of the 2049^2 FP64 oracle ({wall:.1f} s), derivative terms spread over "
+                      f"{workers} worker processes; host {os.cpu_count()} cores"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return None
-    v, cores, wall = _oracle_steps(args.steps, args.warmup)
+    v, cores, wall, workers = _oracle_steps(args.steps, args.warmup)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "points": 2049 * 2049, "precision": "fp64 oracle"},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v,
-                             "sample": f"{args.steps} full Strang steps of the 2049^2 FP64 oracle"},
+                             "sample": f"{args.steps} full Strang steps of the 2049^2 FP64 oracle, derivative terms "
+                                       f"spread over {workers} worker processes"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -486,6 +545,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched, elastic and gradient legs")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the full-run comparison with the golden run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

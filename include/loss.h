@@ -68,9 +68,13 @@ enum {
 };
 
 /* Source kinds (bit mask).  PRESSURE acts on the acoustic pressure, EXPLOSIVE on S11, S22, S33, SHEAR_XZ
- * on S13 (all in the stress sub-step B, evaluated at t_n + dt/2); FORCE_Z is a body force on V3 in each
- * half of the velocity sub-step A (at t_n and t_{n+1}). */
-enum { LOSS_SRC_PRESSURE = 1u, LOSS_SRC_EXPLOSIVE = 2u, LOSS_SRC_SHEAR_XZ = 4u, LOSS_SRC_FORCE_Z = 8u };
+ * on S13 (all in the stress sub-step B, evaluated at t_n + dt/2); FORCE_X, FORCE_Y, FORCE_Z are body forces
+ * f_1, f_2, f_3 of the momentum equation (paper Sec. 2, Eq. conservation_momentum) on V1, V2, V3 in each half of
+ * the velocity sub-step A (at t_n and t_{n+1}); the three together are the paper's source of Sec. 4.3. */
+enum {
+  LOSS_SRC_PRESSURE = 1u, LOSS_SRC_EXPLOSIVE = 2u, LOSS_SRC_SHEAR_XZ = 4u, LOSS_SRC_FORCE_Z = 8u,
+  LOSS_SRC_FORCE_X = 16u, LOSS_SRC_FORCE_Y = 32u
+};
 
 typedef struct {
   int32_t dim;       /* 2 or 3 */
@@ -217,6 +221,7 @@ enum {
                                    LOSS_KERNEL_ACOUSTIC_X) */
   LOSS_KERNEL_ACOUSTIC_Z2 = 10, /* 2-D acoustic FP32 tiles: d_z v3 for the next step (the z velocity part is
                                    LOSS_KERNEL_ACOUSTIC_Z) */
+  LOSS_KERNEL_WATCH = 11,       /* non-finite watchdog pass (loss_set_watchdog) */
   LOSS_NUM_KERNELS = 16
 };
 
@@ -287,21 +292,52 @@ loss_status_t loss_profile(loss_handle_t handle, int32_t enable);
 loss_status_t loss_profile_read(loss_handle_t handle, int32_t kernel, double* total_ms, int64_t* launches);
 
 /* First LOSS derivative along `axis` for callers that cannot allocate device memory (code running under another
- * framework's allocator or memory budget, or inside a stream capture where cudaMalloc is not allowed), so they
- * cannot create a handle.  The paper has no counterpart: this is a deployment variant of loss_derivative.
- * desc: the grid (same rules as loss_create_grid; physics and dt are ignored); f, d1: DEVICE pointers to dense
- * arrays of the grid shape in the working precision of desc->precision; cuda_stream: the stream to run on.
+ * framework's allocator, which owns every device allocation of the process, or under a memory budget that forbids
+ * allocations after start-up), so they cannot create a handle.  The paper has no counterpart: this is a deployment
+ * variant of loss_derivative.
+ * desc: the grid; only dim, n, p, h, n_nb and precision are read and checked as in loss_create_grid (physics and
+ * dt are ignored); f, d1: DEVICE pointers to dense arrays of the grid shape in the working precision of
+ * desc->precision; cuda_stream: the stream to run on.
  * Nothing is allocated: the PMBC weights and Thomas factors are written into a 64 KiB static device array that
  * every GPU loading this library keeps until the process exits.  Limit: (p + 1) * (2 n_nb + 1) <= 8096 on the
  * axis, else LOSS_E_UNSUPPORTED before any work is queued.  Every call rewrites the whole table it reads, so no
- * state carries over between calls, but calls that overlap on the GPU (other streams or devices sharing a
- * context) race on the array: serialise them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.
+ * state carries over between calls; but each device holds one copy of the array, so calls on the same device
+ * whose work overlaps on the GPU (different streams) race on it: serialise them.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.
  * Returns LOSS_E_ARG / LOSS_E_SHAPE for bad arguments, LOSS_E_CUDA if a CUDA call fails. */
 loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis, const void* f, void* d1,
                                       void* cuda_stream);
 
-/* Wait for all work queued on the handle's stream. */
+/* Non-uniform grid spacing along one axis (paper Sec. 3: the construction carries over to non-uniform grids; the
+ * conclusion names it as future work).  x: HOST array of n[axis] + 1 finite, strictly increasing knot coordinates,
+ * copied; NULL returns the axis to the uniform spacing h[axis].  On such an axis loss_derivative (first derivative)
+ * and loss_pmbc_phi use the cubic spline on these knots: the PMBC weights are the junction rows of the global
+ * natural spline's slope operator, truncated to |m| <= n_nb (FP64, built on the host), and each patch solves its
+ * own slope system with the junction values as ends.  Layout and precision of the fields are unchanged.
+ * Returns LOSS_E_ARG for a bad axis or knots; afterwards loss_step, loss_gradient and loss_derivative_adjoint on
+ * the shot, and second derivatives on the axis, return LOSS_E_UNSUPPORTED. */
+loss_status_t loss_set_coordinates(loss_handle_t handle, int32_t shot, int32_t axis, const double* x);
+
+/* Poll limit of the bounded waits of the staged FP32 x kernels (each block waits on an mbarrier for the bulk copies
+ * of its next row).  A wait that runs out sets the handle's device error flag; the block then waits (with a fixed
+ * limit) for its own copies in flight and stops, so the CUDA context stays usable, and the next loss_sync returns
+ * LOSS_E_TIMEOUT and poisons the handle.  polls < 0 restores the default (2^24 polls, far beyond any copy's
+ * latency); polls = 0 makes every such wait give up without polling, which is how the failure path is tested.
+ * This is a library control with no counterpart in the paper.  Takes effect from the next loss_step (a captured
+ * graph is recaptured).  Returns LOSS_E_ARG for a NULL handle. */
+loss_status_t loss_set_wait_limit(loss_handle_t handle, int64_t polls);
+
+/* Non-finite watchdog (a library control with no counterpart in the paper): with every_steps > 0, at the end of
+ * each loss_step call that completes another every_steps steps (counted from this call), one streaming pass over
+ * every field of every shot checks for Inf and NaN (kernel LOSS_KERNEL_WATCH, one read of each field).  The first
+ * non-finite field found is reported by the next loss_sync as LOSS_E_NUMERIC, with the shot and field in
+ * loss_last_error; the report clears the flag and does not poison the handle (fields may be reset with
+ * loss_set_field).  every_steps = 0 (the default) turns the watchdog off.  Returns LOSS_E_ARG for every_steps < 0. */
+loss_status_t loss_set_watchdog(loss_handle_t handle, int64_t every_steps);
+
+/* Wait for all work queued on the handle's stream.  Returns LOSS_E_TIMEOUT (sticky) if a kernel gave up on a
+ * bounded wait, LOSS_E_NUMERIC if the watchdog found a non-finite field, LOSS_E_CUDA if the stream failed. */
 loss_status_t loss_sync(loss_handle_t handle);
 
 #ifdef __cplusplus

@@ -124,15 +124,18 @@ def _Y(op, f, comp, tau, pml, mem, key):
 
 
 def elastic_A(st, mem, op, b, tau, pml, src, t):
-    """v_i += b (sum_j Y_ij + tau f_i); returns {i: sum_j Y_ij} and the force increment of v3 (or None)."""
+    """v_i += b (sum_j Y_ij + tau f_i); returns {i: sum_j Y_ij} and the body-force increments {i: tau f_i} on the
+    source block (empty without a body force)."""
     acc = {}
     for i in (1, 2, 3):
         acc[i] = sum(_Y(op, st[_SIG[(i, j)]], j, tau, pml, mem, f"psi_{i}{j}") for j in (1, 2, 3))
         st[f"v{i}"] = st[f"v{i}"] + b * acc[i]
-    force = None
-    if src is not None and "force_z" in src.kinds:
-        force = tau * ricker(t, src.f0, src.t0) * src.profile
-        st["v3"][src.block] += b[src.block] * force
+    force = {}
+    if src is not None:
+        for i, kind in ((1, "force_x"), (2, "force_y"), (3, "force_z")):
+            if kind in src.kinds:
+                force[i] = tau * ricker(t, src.f0, src.t0) * src.profile
+                st[f"v{i}"][src.block] += b[src.block] * force[i]
     return acc, force
 
 
@@ -233,8 +236,8 @@ def misfit_gradient(w, d_obs: Dict[str, np.ndarray], steps: int, model=None):
             acc2, f2 = elastic_A(st, mem, op, sim.b, 0.5 * dt, pml, src, t_n + dt)
             # transposes in reverse order, with the gradient terms
             g_b += sum(acc2[i] * lam[f"v{i}"] for i in (1, 2, 3))
-            if f2 is not None:
-                g_b[src.block] += f2 * lam["v3"][src.block]
+            for i, fi in f2.items():
+                g_b[src.block] += fi * lam[f"v{i}"][src.block]
             elastic_A_T(lam, lmem, op, sim.b, 0.5 * dt, pml)
             sdiag = lam["s11"] + lam["s22"] + lam["s33"]
             g_lam += (x[1, 1] + x[2, 2] + x[3, 3]) * sdiag
@@ -242,8 +245,8 @@ def misfit_gradient(w, d_obs: Dict[str, np.ndarray], steps: int, model=None):
             g_mu += sum((x[i, j] + x[j, i]) * lam[f"s{i}{j}"] for (i, j) in ((1, 2), (1, 3), (2, 3)))
             elastic_B_T(lam, lmem, op, sim.lam, sim.mu, dt, pml)
             g_b += sum(acc1[i] * lam[f"v{i}"] for i in (1, 2, 3))
-            if f1 is not None:
-                g_b[src.block] += f1 * lam["v3"][src.block]
+            for i, fi in f1.items():
+                g_b[src.block] += fi * lam[f"v{i}"][src.block]
             elastic_A_T(lam, lmem, op, sim.b, 0.5 * dt, pml)
         else:
             X1 = acoustic_A(st, mem, op, sim.b, 0.5 * dt, pml)

@@ -15,8 +15,9 @@ exact as a forward Euler step because its right-hand side does not depend on the
 
 Sources (reading of the garbled Ricker formula in Sec. 4.2): f_r(t) = (1 - 2 (pi f0 (t - t0))^2)
 exp(-(pi f0 (t - t0))^2), with the Gaussian spatial amplitude of Sec. 4.2 (class Source).  Stress sources
-("pressure", "explosive", "shear_xz") act in B and are evaluated at t_n + dt/2; a body force ("force_z")
-acts in each half of A, at t_n and at t_{n+1}.
+("pressure", "explosive", "shear_xz") act in B and are evaluated at t_n + dt/2; body forces ("force_x",
+"force_y", "force_z": f_1, f_2, f_3 of Eq. conservation_momentum, each A(x) f_r(t)) act in each half of A, at
+t_n and at t_{n+1}.
 
 Absorbing layer (Sec. 3.3): an ADE-PML in the outer points of every axis with the exponential Strang
 splitting of the paper (class PML).  Without it the natural-spline ends impose no physical boundary condition
@@ -228,8 +229,10 @@ def elastic_half_A(st, op, b, tau, src: Optional[Source], t, pml: Optional[PML] 
     for i in (1, 2, 3):
         acc = sum(_tau_deriv(op, st[_SIG[(i, j)]], j, tau, pml, mem, f"psi_{i}{j}") for j in (1, 2, 3))
         st[f"v{i}"] = st[f"v{i}"] + b * acc
-    if src is not None and "force_z" in src.kinds:
-        st["v3"][src.block] += tau * b[src.block] * ricker(t, src.f0, src.t0) * src.profile
+    if src is not None:
+        for i, kind in ((1, "force_x"), (2, "force_y"), (3, "force_z")):
+            if kind in src.kinds:
+                st[f"v{i}"][src.block] += tau * b[src.block] * ricker(t, src.f0, src.t0) * src.profile
 
 
 def elastic_B(st, op, lam, mu, dt, src: Optional[Source], t_half, pml: Optional[PML] = None, mem=None):

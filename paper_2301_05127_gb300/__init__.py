@@ -22,11 +22,12 @@ LOSS_OK, LOSS_E_ARG, LOSS_E_SHAPE, LOSS_E_NOMEM, LOSS_E_CUDA, LOSS_E_STATE, LOSS
 LOSS_ACOUSTIC, LOSS_ELASTIC = 0, 1
 LOSS_FP64, LOSS_FP32, LOSS_FP32_KAHAN = 0, 1, 2
 LOSS_MEM_HOST, LOSS_MEM_DEVICE = 0, 1
-LOSS_SRC_PRESSURE, LOSS_SRC_EXPLOSIVE, LOSS_SRC_SHEAR_XZ, LOSS_SRC_FORCE_Z = 1, 2, 4, 8
+LOSS_SRC_PRESSURE, LOSS_SRC_EXPLOSIVE, LOSS_SRC_SHEAR_XZ, LOSS_SRC_FORCE_Z, LOSS_SRC_FORCE_X, LOSS_SRC_FORCE_Y = \
+    1, 2, 4, 8, 16, 32
 FIELDS = {"v1": 0, "v2": 1, "v3": 2, "s11": 3, "s22": 4, "s33": 5, "s12": 6, "s13": 7, "s23": 8, "sigma": 3}
 PRECISIONS = {"fp64": LOSS_FP64, "fp32": LOSS_FP32, "fp32_kahan": LOSS_FP32_KAHAN}
 SOURCE_KINDS = {"pressure": LOSS_SRC_PRESSURE, "explosive": LOSS_SRC_EXPLOSIVE, "shear_xz": LOSS_SRC_SHEAR_XZ,
-                "force_z": LOSS_SRC_FORCE_Z}
+                "force_z": LOSS_SRC_FORCE_Z, "force_x": LOSS_SRC_FORCE_X, "force_y": LOSS_SRC_FORCE_Y}
 
 
 class GridDesc(ctypes.Structure):
@@ -84,9 +85,12 @@ _PROTOS = {
     "loss_autotune": (_I32, [_H, _I32, ctypes.POINTER(TuneEntry), _I32, ctypes.POINTER(_I32)]),
     "loss_profile": (_I32, [_H, _I32]),
     "loss_profile_read": (_I32, [_H, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "loss_set_wait_limit": (_I32, [_H, _I64]),
+    "loss_set_watchdog": (_I32, [_H, _I64]),
+    "loss_set_coordinates": (_I32, [_H, _I32, _I32, _P]),
 }
 KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
-           "elastic_z": 6, "clock": 7, "adjoint": 8, "acoustic_x2": 9, "acoustic_z2": 10}
+           "elastic_z": 6, "clock": 7, "adjoint": 8, "acoustic_x2": 9, "acoustic_z2": 10, "watch": 11}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -397,6 +401,24 @@ class Grid:
         kid = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         _check(lib().loss_profile_read(self.h, kid, ctypes.byref(ms), ctypes.byref(n)), self.h)
         return ms.value, n.value
+
+    def set_coordinates(self, shot, axis, x):
+        """Knot coordinates of a non-uniform axis (n + 1 increasing values), or None for uniform spacing
+        (loss_set_coordinates)."""
+        if x is None:
+            _check(lib().loss_set_coordinates(self.h, shot, axis, None), self.h)
+            return
+        xs = np.ascontiguousarray(x, dtype=np.float64)
+        _check(lib().loss_set_coordinates(self.h, shot, axis, xs.ctypes.data), self.h)
+
+    def set_wait_limit(self, polls: int = -1):
+        """Poll limit of the staged x kernels' bounded waits (-1 = default, 0 = give up at once)
+        (loss_set_wait_limit)."""
+        _check(lib().loss_set_wait_limit(self.h, int(polls)), self.h)
+
+    def set_watchdog(self, every_steps: int):
+        """Non-finite check of every field every ``every_steps`` steps (0 = off) (loss_set_watchdog)."""
+        _check(lib().loss_set_watchdog(self.h, int(every_steps)), self.h)
 
     def sync(self):
         _check(lib().loss_sync(self.h), self.h)

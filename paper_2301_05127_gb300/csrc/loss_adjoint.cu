@@ -394,7 +394,7 @@ loss_status_t run_gradient(loss_ctx* h, Shot& s, const double* d_obs, int32_t ch
   if (s.n_rcv == 0) return err(h, LOSS_E_STATE, "the shot has no receivers");
   if (!(s.d.physics == LOSS_ELASTIC || (s.d.physics == LOSS_ACOUSTIC && s.dim == 2)))
     return err(h, LOSS_E_UNSUPPORTED, "gradients are built for 2-D acoustic and 3-D elastic grids");
-  if (s.src_on && (s.src_kinds & LOSS_SRC_FORCE_Z))
+  if (s.src_on && (s.src_kinds & kForceMask))
     return err(h, LOSS_E_UNSUPPORTED, "gradients with a body-force source are not built");
   if (!d_obs || !misfit || !g_vp || !g_rho || (s.d.physics == LOSS_ELASTIC && !g_vs))
     return err(h, LOSS_E_ARG, "null argument");

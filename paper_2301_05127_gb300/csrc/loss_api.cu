@@ -501,9 +501,10 @@ loss_status_t loss_create_grid(const loss_grid_desc_t* descs, int32_t n_shots, c
       cudaMemcpyAsync(h->t32, t32.data(), kTableLen * sizeof(float), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess)
     return bail(LOSS_E_CUDA);
-  if (dev_alloc(h, sizeof(int), (void**)&h->dflag) != LOSS_OK ||
-      cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) != cudaSuccess)
+  if (dev_alloc(h, 2 * sizeof(int), (void**)&h->dflag) != LOSS_OK ||
+      cudaMemsetAsync(h->dflag, 0, 2 * sizeof(int), h->stream) != cudaSuccess)
     return bail(LOSS_E_NOMEM);
+  h->nflag = h->dflag + 1;
   h->shots.resize(n_shots);
   for (int i = 0; i < n_shots; ++i) {
     h->shots[i].d = descs[i];
@@ -703,9 +704,45 @@ loss_status_t loss_profile_read(loss_handle_t h, int32_t kernel, double* total_m
 loss_status_t loss_sync(loss_handle_t h) {
   LOSS_TRY(guard(h));
   LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize"));
-  int flag = 0;
-  if (h->dflag) LOSS_TRY(cuda_check(h, cudaMemcpy(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost), "read flag"));
-  if (flag) return fail(h, LOSS_E_TIMEOUT, "a kernel gave up waiting for its staged data");
+  int flag[2] = {0, 0};
+  if (h->dflag)
+    LOSS_TRY(cuda_check(h, cudaMemcpy(flag, h->dflag, 2 * sizeof(int), cudaMemcpyDeviceToHost), "read flags"));
+  if (flag[0]) return fail(h, LOSS_E_TIMEOUT, "a kernel gave up waiting for its staged data");
+  if (flag[1]) {
+    LOSS_TRY(cuda_check(h, cudaMemsetAsync(h->nflag, 0, sizeof(int), h->stream), "clear flag"));
+    LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize"));
+    const int shot = (flag[1] - 1) / LOSS_NUM_FIELDS, field = (flag[1] - 1) % LOSS_NUM_FIELDS;
+    return fail(h, LOSS_E_NUMERIC,
+                "non-finite value in shot " + std::to_string(shot) + ", field " + std::to_string(field));
+  }
+  return LOSS_OK;
+}
+
+loss_status_t loss_set_wait_limit(loss_handle_t h, int64_t polls) {
+  LOSS_TRY(guard(h));
+  h->wait_polls = polls < 0 ? (1u << 24) : (unsigned)std::min<int64_t>(polls, 0xffffffffLL);
+  return LOSS_OK;
+}
+
+loss_status_t loss_set_watchdog(loss_handle_t h, int64_t every_steps) {
+  LOSS_TRY(guard(h));
+  if (every_steps < 0) return fail(h, LOSS_E_ARG, "every_steps must be >= 0");
+  h->watch_every = every_steps;
+  h->watch_count = 0;
+  return LOSS_OK;
+}
+
+// One watchdog pass over every field of every shot (loss_set_watchdog).
+static loss_status_t watch_fields(loss_ctx* h) {
+  for (size_t i = 0; i < h->shots.size(); ++i) {
+    Shot& s = h->shots[i];
+    for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {
+      if (!field_used(s, f)) continue;
+      LaunchScope ls(h, LOSS_KERNEL_WATCH);
+      LOSS_TRY(cuda_check(h, launch_finite(s.field[f], s.total, s.esize, h->nflag, 1 + (int)i * LOSS_NUM_FIELDS + f,
+                                           h->num_sms, h->stream), "watchdog"));
+    }
+  }
   return LOSS_OK;
 }
 
@@ -795,7 +832,7 @@ loss_status_t loss_set_source(loss_handle_t h, int32_t shot, const int64_t idx[3
   }
   if (!idx) return fail(h, LOSS_E_ARG, "null source index");
   const uint32_t allowed = s->d.physics == LOSS_ELASTIC
-                               ? (LOSS_SRC_EXPLOSIVE | LOSS_SRC_SHEAR_XZ | LOSS_SRC_FORCE_Z)
+                               ? (LOSS_SRC_EXPLOSIVE | LOSS_SRC_SHEAR_XZ | kForceMask)
                                : LOSS_SRC_PRESSURE;
   if (kind_mask & ~allowed) return fail(h, LOSS_E_ARG, "source kind not valid for this physics");
   int64_t c[3];
@@ -975,10 +1012,22 @@ loss_status_t loss_step(loss_handle_t h, int64_t n_steps) {
   for (Shot& s : h->shots) {
     if (!s.has_model) return fail(h, LOSS_E_STATE, "loss_set_model must be called for every shot before stepping");
   }
+  for (Shot& s : h->shots)
+    if (any_nonuniform(s)) return fail(h, LOSS_E_UNSUPPORTED, "time steps on non-uniform grids are not built");
   for (Shot& s : h->shots) LOSS_TRY(ensure_trace_capacity(h, s, s.rcv_steps + n_steps));
-  if (batch_eligible(h)) return step_batched(h, n_steps);
-  for (int64_t k = 0; k < n_steps; ++k) {
-    for (Shot& s : h->shots) LOSS_TRY(step_shot(h, s));
+  if (batch_eligible(h)) {
+    LOSS_TRY(step_batched(h, n_steps));
+  } else {
+    for (int64_t k = 0; k < n_steps; ++k) {
+      for (Shot& s : h->shots) LOSS_TRY(step_shot(h, s));
+    }
+  }
+  if (h->watch_every > 0) {
+    h->watch_count += n_steps;
+    if (h->watch_count >= h->watch_every) {
+      h->watch_count %= h->watch_every;
+      LOSS_TRY(watch_fields(h));
+    }
   }
   return LOSS_OK;
 }
@@ -1015,10 +1064,18 @@ loss_status_t loss_derivative(loss_handle_t h, int32_t shot, int32_t axis, const
   return run_derivative(h, *s, axis_slot(*s, axis), f, d1, d2, nullptr, mem);
 }
 
+loss_status_t loss_set_coordinates(loss_handle_t h, int32_t shot, int32_t axis, const double* x) {
+  Shot* s;
+  LOSS_TRY(get_shot(h, shot, &s));
+  if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
+  return set_coordinates(h, *s, axis_slot(*s, axis), x);
+}
+
 loss_status_t loss_derivative_adjoint(loss_handle_t h, int32_t shot, int32_t axis, const void* g, void* out,
                                       int32_t mem) {
   Shot* s;
   LOSS_TRY(get_shot(h, shot, &s));
+  if (any_nonuniform(*s)) return fail(h, LOSS_E_UNSUPPORTED, "adjoints on non-uniform grids are not built");
   if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
   if (!g || !out || (mem != LOSS_MEM_HOST && mem != LOSS_MEM_DEVICE)) return fail(h, LOSS_E_ARG, "bad buffers");
   return run_derivative_adjoint(h, *s, axis_slot(*s, axis), g, out, mem);
@@ -1028,6 +1085,7 @@ loss_status_t loss_gradient(loss_handle_t h, int32_t shot, const double* d_obs, 
                             int64_t n_steps, double* misfit, double* g_vp, double* g_vs, double* g_rho, int32_t mem) {
   Shot* s;
   LOSS_TRY(get_shot(h, shot, &s));
+  if (any_nonuniform(*s)) return fail(h, LOSS_E_UNSUPPORTED, "gradients on non-uniform grids are not built");
   return run_gradient(h, *s, d_obs, checkpoint_every, n_steps, misfit, g_vp, g_vs, g_rho, mem);
 }
 
@@ -1162,6 +1220,10 @@ static Tables tables_for(loss_ctx* h, const Shot& s, int k) {
 
 template <typename T>
 static loss_status_t run_derivative_t(loss_ctx* h, Shot& s, int k, const T* f, T* d1, T* d2, double* phi) {
+  if (s.nu_tab[k]) {
+    if (d2) return fail(h, LOSS_E_UNSUPPORTED, "second derivatives on non-uniform axes are not built");
+    return run_nu_derivative<T>(h, s, k, f, d1, phi);
+  }
   const int64_t sy = s.len[2], sz = s.len[2] * s.len[1];
   LineGeom g;
   int logc, threads;

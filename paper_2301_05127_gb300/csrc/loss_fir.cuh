@@ -113,6 +113,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 // Orders this thread's earlier generic shared-memory accesses before later bulk copies into the same memory.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Poll limit of the waits that drain a block's own copies in flight after another wait gave up.  The copies were
+// issued by the block and complete without it, so this limit only bounds the exit path.
+constexpr unsigned kDrainPolls = 1u << 24;
 // Waits until the phase with parity `parity` of the barrier has completed; gives up after `limit` polls and then
 // returns false (the caller records the failure and stops).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit) {

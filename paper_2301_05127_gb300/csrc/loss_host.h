@@ -12,6 +12,12 @@
 namespace lossk {
 
 constexpr int kTableLen = 64;
+// Body-force source kinds (f_1, f_2, f_3) and the component of each.
+constexpr uint32_t kForceMask = LOSS_SRC_FORCE_X | LOSS_SRC_FORCE_Y | LOSS_SRC_FORCE_Z;
+inline int force_components(uint32_t kinds) {
+  return ((kinds & LOSS_SRC_FORCE_X) ? 1 : 0) | ((kinds & LOSS_SRC_FORCE_Y) ? 2 : 0) |
+         ((kinds & LOSS_SRC_FORCE_Z) ? 4 : 0);
+}
 
 // One independent grid (shot).  Internal axis slots: 0 = z, 1 = y, 2 = x; 2-D grids have a y extent of 1.
 // Device arrays use a padded layout: x pitch px (multiple of 32 elements), y stride sy = px, z stride sz.
@@ -32,6 +38,7 @@ struct Shot {
   void* tmp[8] = {};     // derivative temporaries (acoustic: tmp[0] = d_z v3)
   double* W[3] = {};     // PMBC weights per axis slot, scaled by h/3
   double* Wd[3] = {};     // junction-correction weights of the FP32 truncated-convolution kernels (on first use)
+  void* nu_tab[3] = {};   // non-uniform axis slot (loss_set_coordinates): PMBC weights and elimination tables
   bool has_model = false;
   double vmax = 0.0;
   bool b_const = false;  // density constant: buoyancy passed as a scalar, the b array is not read
@@ -134,6 +141,11 @@ struct loss_ctx {
   int batched = 1;       // several 2-D acoustic shots: one persistent launch per kernel over all of them
   int tiled = 1;         // FP32 2-D acoustic shots stepped one at a time: truncated-convolution tile kernels
   int* dflag = nullptr;  // device error flag of kernels with bounded waits (read by loss_sync)
+  unsigned wait_polls = 1u << 24;  // poll limit of those waits (loss_set_wait_limit)
+  // non-finite watchdog (loss_set_watchdog): every watch_every steps (0 = off) a check of every field sets nflag to
+  // 1 + shot * LOSS_NUM_FIELDS + field of the first non-finite field found (read and cleared by loss_sync)
+  int64_t watch_every = 0, watch_count = 0;
+  int* nflag = nullptr;
   int graph_steps = 0;   // > 0: steps are replayed from a captured CUDA graph of this many steps
   bool capturing = false;
   lossk::BatchState batch;
@@ -161,6 +173,11 @@ loss_status_t validate(const loss_grid_desc_t& d, std::string* why);
 bool is_velocity(int f);
 loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows);
 loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d1, void* d2, double* phi, int mem);
+// loss_nonuniform.cu
+template <typename T>
+loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi);
+loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x);
+inline bool any_nonuniform(const Shot& s) { return s.nu_tab[0] || s.nu_tab[1] || s.nu_tab[2]; }
 // loss_adjoint.cu
 loss_status_t run_derivative_adjoint(loss_ctx* h, Shot& s, int k, const void* g, void* out, int mem);
 loss_status_t run_gradient(loss_ctx* h, Shot& s, const double* d_obs, int32_t checkpoint_every, int64_t n_steps,
@@ -223,18 +240,20 @@ cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshot
 template <typename T>
 cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
 cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
+// loss_watch.cu: sets *flag to code (if it is still 0) when one of the n values at f is not finite
+cudaError_t launch_finite(const void* f, int64_t n, size_t esize, int* flag, int code, int num_sms, cudaStream_t st);
 template <bool KAHAN>
 cudaError_t launch_tz(const AcZArgs<float>& a, const TileGeom& t, int mode, int threads, int logc, cudaStream_t st);
 template <bool KAHAN>
-cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
-                      cudaStream_t st);
+cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, unsigned polls,
+                      int num_sms, cudaStream_t st);
 size_t tile_smem_z(const TileGeom& t, int mode, int logc);
 size_t xp_smem(const TileGeom& t, bool kahan);
 int xp_rows_per_unit(int n, int threads);
 XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& rs, bool kahan);
 template <bool KAHAN>
 cudaError_t launch_xp_batch(const XpShot* shots, const int* unit0, const int* bunit, const int* bshot,
-                            const XpSmem& L, int threads, int grid, int* err, cudaStream_t st);
+                            const XpSmem& L, int threads, int grid, int* err, unsigned polls, cudaStream_t st);
 template <bool KAHAN>
 cudaError_t xp_batch_per_sm(const XpSmem& L, int threads, int* per_sm);
 template <bool KAHAN>

@@ -213,12 +213,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
       const T b = a.b ? a.b[gi] : a.b0;
-      T force = T(0);  // body force f_3 (FORCE_Z source), already multiplied by the sub-step length
+      T force = T(0);  // body force (FORCE_X/Y/Z sources), already multiplied by the sub-step length
       if (a.srcp.on) {
         const int dz = outer - a.srcp.zs + 12, dy = pos - a.srcp.ys + 12, dx = x0 + l - a.srcp.xs + 12;
         if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u)
           force = (T)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
       }
+      const T f0 = (a.force_mask & 1) ? force : T(0), f1 = (a.force_mask & 2) ? force : T(0),
+              f2 = (a.force_mask & 4) ? force : T(0);
       T u[3], cu[3];
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
@@ -226,9 +228,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
         cu[f] = KAHAN ? a.cmp[LOSS_FIELD_V1 + f][gi] : T(0);
       }
       const T t5 = t[5][gi], t6 = t[6][gi], t7 = t[7][gi];
-      const T d0 = b * (t5 + effA(a, 0, gi, pos, a.s3h * O[0][k], ta));
-      const T d1 = b * (t6 + effA(a, 1, gi, pos, a.s3h * O[1][k], ta));
-      const T d2 = b * (t7 + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + force);
+      const T d0 = b * (t5 + effA(a, 0, gi, pos, a.s3h * O[0][k], ta) + f0);
+      const T d1 = b * (t6 + effA(a, 1, gi, pos, a.s3h * O[1][k], ta) + f1);
+      const T d2 = b * (t7 + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + f2);
       upd_r<T, KAHAN>(u[0], cu[0], d0);
       upd_r<T, KAHAN>(u[1], cu[1], d1);
       upd_r<T, KAHAN>(u[2], cu[2], d2);

@@ -881,7 +881,8 @@ __device__ __forceinline__ void xp_init_barriers(uint64_t* bar) {
 // current row, so HBM streams while the block computes.  Waits on the stage barriers are bounded: on a timeout
 // the block records it in *err, waits (bounded) for its copy in flight and stops.
 template <bool KAHAN>
-__global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic, int* err) {
+__global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic, int* err,
+                                                unsigned polls) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float rpow[kFirPow];
   __shared__ float dlf[65];
@@ -925,12 +926,12 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
       fence_proxy_async();
       issue(row + G, st ^ 1, split ? 2 : 0);
     }
-    const bool ok = mbar_wait(&bar[st], parity[st], 1u << 24);
+    const bool ok = mbar_wait(&bar[st], parity[st], polls);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {  // let the copies in flight land (bounded) before the block leaves
         atomicExch(err, 1);
-        mbar_wait(&bar[st], parity[st], 1u << 24);
-        if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], 1u << 24);
+        mbar_wait(&bar[st], parity[st], kDrainPolls);
+        if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], kDrainPolls);
       }
       return;
     }
@@ -961,7 +962,7 @@ __global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, uns
 template <bool KAHAN>
 __global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ shots, const int* __restrict__ unit0,
                                                      const int* __restrict__ bunit, const int* __restrict__ bshot,
-                                                     XpSmem L, int* err) {
+                                                     XpSmem L, int* err, unsigned polls) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float rpow[kFirPow];
   __shared__ __align__(8) uint64_t bar[2];
@@ -1034,11 +1035,12 @@ __global__ void __launch_bounds__(256, 2) k_xp_batch(const XpShot* __restrict__ 
       fence_proxy_async();
       issue(u + 1, st ^ 1);
     }
-    const bool ok = mbar_wait(&bar[st], parity[st], 1u << 24);
+    const bool ok = mbar_wait(&bar[st], parity[st], polls);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0) {  // let the copies in flight land (bounded) before the block leaves
         atomicExch(err, 1);
-        if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], 1u << 24);
+        mbar_wait(&bar[st], parity[st], kDrainPolls);
+        if (more) mbar_wait(&bar[st ^ 1], parity[st ^ 1], kDrainPolls);
       }
       return;
     }
@@ -1140,10 +1142,10 @@ XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& 
 
 template <bool KAHAN>
 cudaError_t launch_xp_batch(const XpShot* shots, const int* unit0, const int* bunit, const int* bshot,
-                            const XpSmem& L, int threads, int grid, int* err, cudaStream_t st) {
+                            const XpSmem& L, int threads, int grid, int* err, unsigned polls, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   XpSmem l = L;
-  void* argv[] = {(void*)&shots, (void*)&unit0, (void*)&bunit, (void*)&bshot, (void*)&l, (void*)&err};
+  void* argv[] = {(void*)&shots, (void*)&unit0, (void*)&bunit, (void*)&bshot, (void*)&l, (void*)&err, (void*)&polls};
   return tile_launch(k_xp_batch<KAHAN>, grid, threads, (size_t)L.total * 4, st, argv);
 }
 template <bool KAHAN>
@@ -1172,9 +1174,9 @@ cudaError_t tz_batch_per_sm(int mode, int threads, int logc, size_t smem, int* p
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
 }
 template cudaError_t launch_xp_batch<false>(const XpShot*, const int*, const int*, const int*, const XpSmem&, int, int,
-                                            int*, cudaStream_t);
+                                            int*, unsigned, cudaStream_t);
 template cudaError_t launch_xp_batch<true>(const XpShot*, const int*, const int*, const int*, const XpSmem&, int, int,
-                                           int*, cudaStream_t);
+                                           int*, unsigned, cudaStream_t);
 template cudaError_t xp_batch_per_sm<false>(const XpSmem&, int, int*);
 template cudaError_t xp_batch_per_sm<true>(const XpSmem&, int, int*);
 template cudaError_t launch_tz_batch<false>(const TzShot*, const int*, int, int, int, int, int, size_t, int,
@@ -1185,19 +1187,22 @@ template cudaError_t tz_batch_per_sm<false>(int, int, int, size_t, int*);
 template cudaError_t tz_batch_per_sm<true>(int, int, int, size_t, int*);
 
 template <bool KAHAN>
-cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, int num_sms,
-                      cudaStream_t st) {
+cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, unsigned polls,
+                      int num_sms, cudaStream_t st) {
   AcXArgs<float> aa = a;
   TileGeom tt = t;
   unsigned mm = mmagic;
   int* e = err;
-  void* argv[] = {&aa, &tt, &mm, &e};
+  unsigned pl = polls;
+  void* argv[] = {&aa, &tt, &mm, &e, &pl};
   const int threads = (((t.n + 7) / 8 + 31) / 32) * 32;
   const int grid = t.ncross < 2 * num_sms ? t.ncross : 2 * num_sms;
   return tile_launch(k_xp<KAHAN>, grid, threads, xp_smem(t, KAHAN), st, argv);
 }
-template cudaError_t launch_xp<false>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);
-template cudaError_t launch_xp<true>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, int, cudaStream_t);
+template cudaError_t launch_xp<false>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, unsigned, int,
+                                      cudaStream_t);
+template cudaError_t launch_xp<true>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, unsigned, int,
+                                     cudaStream_t);
 
 template cudaError_t launch_tz<false>(const AcZArgs<float>&, const TileGeom&, int, int, int, cudaStream_t);
 template cudaError_t launch_tz<true>(const AcZArgs<float>&, const TileGeom&, int, int, int, cudaStream_t);

@@ -85,12 +85,14 @@ struct Tab<double> {
 };
 
 // FP32 -> FP64 widening on the integer units (IEEE 754: binary32 exponent bias 127, binary64 bias 1023, the 23
-// fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0.
-// Keeps the FP64 pipe, which is narrow on this GPU, free for the FMAs of the junction sums.
+// fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0;
+// the all-ones exponent (Inf, NaN) maps to the all-ones binary64 exponent, so a diverged field stays Inf / NaN in
+// the FP64 sums.  Keeps the FP64 pipe, which is narrow on this GPU, free for the FMAs of the junction sums.
 __device__ __forceinline__ double widen(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ex = (u >> 23) & 0xffu;
-  const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned ex64 = ex == 0xffu ? 0x7ffu : ex + 896u;
+  const unsigned hi = (u & 0x80000000u) | (ex64 << 20) | ((u & 0x7fffffu) >> 3);
   return ex ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
 }
 

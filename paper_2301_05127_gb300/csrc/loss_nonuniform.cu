@@ -1,0 +1,267 @@
+// LOSS derivative on an axis with non-uniform grid spacing.
+//
+// The paper develops LOSS on a uniform grid and notes that the construction carries over to non-uniform grids
+// (Sec. 3, and the future work of its conclusion).  On knots x_0 < ... < x_N the cubic spline through the samples
+// is described here by its knot slopes d_i = s'(x_i), which is equivalent to the B-spline coefficients of the paper
+// (the spline restricted to a patch is fixed by its samples and its two end slopes):
+//
+//   - C^2 continuity at an interior knot i gives the slope equation
+//       h_i d_{i-1} + 2 (h_{i-1} + h_i) d_i + h_{i-1} d_{i+1} = a_i (f_i - f_{i-1}) + b_i (f_{i+1} - f_i),
+//     with h_i = x_{i+1} - x_i, a_i = 3 h_i / h_{i-1}, b_i = 3 h_{i-1} / h_i (uniform grid: d_{i-1} + 4 d_i + d_{i+1}
+//     = 3 (f_{i+1} - f_{i-1}) / h);
+//   - the natural end conditions s''(x_0) = s''(x_N) = 0 give 2 d_0 + d_1 = 3 (f_1 - f_0) / h_0 and
+//     d_{N-1} + 2 d_N = 3 (f_N - f_{N-1}) / h_{N-1}.
+//
+// PMBC weights (Eqs. PMBC, PMBC_coeffcients): the junction slope of the global spline is row jM of T^{-1} R (T the
+// slope matrix, R the right-hand-side operator), computed in FP64 on the host by one tridiagonal solve with T^T per
+// junction and truncated to |m| <= n_nb (one-sided at the ends).  The local solve of each patch is the slope system
+// of its interior knots with the junction values phi as Dirichlet ends, by Thomas elimination with per-position
+// factors (the patch matrices differ, so there is no shared factor table).  Samples of the PMBC sums are
+// accumulated in FP64.
+//
+// One thread per (grid line, patch): it forms both junction sums, sweeps forward writing the eliminated right-hand
+// side into the output line, and sweeps back.  Consecutive threads take consecutive lines of the same patch, so
+// lines along y and z (consecutive x) load and store coalesced; lines along x are walked by each thread alone.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "loss_host.h"
+
+namespace lossk {
+
+#define NU_TRY(expr)                \
+  do {                              \
+    loss_status_t st_ = (expr);     \
+    if (st_ != LOSS_OK) return st_; \
+  } while (0)
+
+static loss_status_t fail_msg(loss_ctx* h, loss_status_t st, const std::string& msg) {
+  h->err = msg;
+  return st;
+}
+
+// Host: FP64 tables of one non-uniform axis.  W: [(p + 1)][2 n_nb + 1] PMBC weights.  Per knot i: A = h_i,
+// G = h_{i-1} (the off-diagonal coefficients), L = the forward-elimination multiplier (0 at a patch's first
+// interior knot), IU = 1 / pivot, a_i, b_i (right-hand side); entries at junctions are unused.
+struct NuHost {
+  std::vector<double> W, A, G, L, IU, ra, rb;
+};
+
+static bool nu_tables(const std::vector<double>& x, int p, int n_nb, NuHost* t, std::string* why) {
+  const int N = (int)x.size() - 1;
+  if (N < 2 || N % p) return *why = "bad knot count", false;
+  std::vector<double> h(N);
+  for (int i = 0; i < N; ++i) {
+    h[i] = x[i + 1] - x[i];
+    if (!(h[i] > 0.0) || !std::isfinite(h[i])) return *why = "knots must be finite and strictly increasing", false;
+  }
+  const int M = N / p;
+  // Global slope system T d = R f: sub (lo), diagonal (di), super (up) of T; R row i has entries at i - 1, i, i + 1.
+  std::vector<double> lo(N + 1, 0.0), di(N + 1), up(N + 1, 0.0), rm(N + 1, 0.0), r0(N + 1, 0.0), rp(N + 1, 0.0);
+  di[0] = 2.0, up[0] = 1.0, r0[0] = -3.0 / h[0], rp[0] = 3.0 / h[0];
+  di[N] = 2.0, lo[N] = 1.0, rm[N] = -3.0 / h[N - 1], r0[N] = 3.0 / h[N - 1];
+  for (int i = 1; i < N; ++i) {
+    lo[i] = h[i];
+    di[i] = 2.0 * (h[i - 1] + h[i]);
+    up[i] = h[i - 1];
+    const double a = 3.0 * h[i] / h[i - 1], b = 3.0 * h[i - 1] / h[i];
+    rm[i] = -a, r0[i] = a - b, rp[i] = b;
+  }
+  // Row c of T^{-1} R: solve T^T y = e_c (T^T has sub-diagonal up[i - 1] and super-diagonal lo[i + 1]), then
+  // w_j = sum_i y_i R_{i, j}.
+  const int wl = 2 * n_nb + 1;
+  t->W.assign((size_t)(p + 1) * wl, 0.0);
+  std::vector<double> cp(N + 1), y(N + 1);
+  for (int j = 0; j <= p; ++j) {
+    const int c = j * M;
+    // Thomas on T^T: row i reads y_{i-1} up[i-1] + y_i di[i] + y_{i+1} lo[i+1] = delta_{ic}
+    double den = di[0];
+    cp[0] = (N > 0 ? lo[1] : 0.0) / den;
+    y[0] = (c == 0 ? 1.0 : 0.0) / den;
+    for (int i = 1; i <= N; ++i) {
+      const double sub = up[i - 1];
+      den = di[i] - sub * cp[i - 1];
+      cp[i] = (i < N ? lo[i + 1] : 0.0) / den;
+      y[i] = ((i == c ? 1.0 : 0.0) - sub * y[i - 1]) / den;
+    }
+    for (int i = N - 1; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
+    const int mlo = (j == 0) ? 0 : -n_nb, mhi = (j == p) ? 0 : n_nb;
+    for (int m = mlo; m <= mhi; ++m) {
+      const int col = c + m;
+      if (col < 0 || col > N) continue;
+      double w = 0.0;  // (R^T y)_col = y_{col+1} R_{col+1,col} + y_col R_{col,col} + y_{col-1} R_{col-1,col}
+      if (col + 1 <= N) w += y[col + 1] * rm[col + 1];
+      w += y[col] * r0[col];
+      if (col - 1 >= 0) w += y[col - 1] * rp[col - 1];
+      t->W[(size_t)j * wl + (m + n_nb)] = w;
+    }
+  }
+  // Local elimination tables of the patch systems (interior knots lM + 1 .. (l + 1)M - 1).
+  t->A.assign(N + 1, 0.0), t->G.assign(N + 1, 0.0), t->L.assign(N + 1, 0.0), t->IU.assign(N + 1, 0.0);
+  t->ra.assign(N + 1, 0.0), t->rb.assign(N + 1, 0.0);
+  for (int l = 0; l < p; ++l) {
+    double u_prev = 0.0;
+    for (int i = l * M + 1; i < (l + 1) * M; ++i) {
+      t->A[i] = h[i];
+      t->G[i] = h[i - 1];
+      t->ra[i] = 3.0 * h[i] / h[i - 1];
+      t->rb[i] = 3.0 * h[i - 1] / h[i];
+      const double d = 2.0 * (h[i - 1] + h[i]);
+      if (i == l * M + 1) {
+        t->L[i] = 0.0;
+        u_prev = d;
+      } else {
+        t->L[i] = h[i] / u_prev;
+        u_prev = d - t->L[i] * h[i - 2];  // the previous knot's super-diagonal is G_{i-1} = h_{i-2}
+      }
+      t->IU[i] = 1.0 / u_prev;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+struct NuArgs {
+  const T* f;
+  T* d1;
+  double* phi;       // [lines][p + 1] or null
+  const double* W;   // [(p + 1)][2 n_nb + 1]
+  const T* tab;      // A, G, L, IU, ra, rb: 6 x (n + 1)
+  int64_t lines, stride;
+  int64_t outer_stride;  // base of line q: (q / inner) * outer_stride + (q % inner) * inner_mul
+  int64_t inner, inner_mul;
+  int n, p, M, n_nb;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_nu_deriv(NuArgs<T> a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.lines * a.p) return;
+  const int l = (int)(tid / a.lines);
+  const int64_t q = tid - (int64_t)l * a.lines;
+  const int64_t base = (q / a.inner) * a.outer_stride + (q % a.inner) * a.inner_mul;
+  const T* f = a.f + base;
+  const int64_t s = a.stride;
+  const int wl = 2 * a.n_nb + 1;
+  auto phi_sum = [&](int j) {
+    const int c = j * a.M;
+    const int mlo = max(-a.n_nb, -c), mhi = min(a.n_nb, a.n - c);
+    const double* w = a.W + (size_t)j * wl + a.n_nb;
+    double acc = 0.0;
+    for (int m = mlo; m <= mhi; ++m) acc = fma(w[m], (double)f[(c + m) * s], acc);
+    return acc;
+  };
+  const double phL = phi_sum(l), phR = phi_sum(l + 1);
+  if (a.phi) {
+    a.phi[q * (a.p + 1) + l] = phL;
+    if (l == a.p - 1) a.phi[q * (a.p + 1) + a.p] = phR;
+  }
+  if (!a.d1) return;
+  T* d = a.d1 + base;
+  const int np = a.n + 1;
+  const T* A = a.tab;
+  const T* G = A + np;
+  const T* L = G + np;
+  const T* IU = L + np;
+  const T* RA = IU + np;
+  const T* RB = RA + np;
+  const int c0 = l * a.M, c1 = c0 + a.M;
+  T fm = f[c0 * s], f0 = f[(c0 + 1) * s];
+  T y = T(0);
+  for (int i = c0 + 1; i < c1; ++i) {
+    const T fp = f[(i + 1) * s];
+    T r = RA[i] * (f0 - fm) + RB[i] * (fp - f0);
+    if (i == c0 + 1) r -= A[i] * (T)phL;
+    if (i == c1 - 1) r -= G[i] * (T)phR;
+    y = r - L[i] * y;
+    d[i * s] = y;
+    fm = f0;
+    f0 = fp;
+  }
+  T dn = T(0);
+  for (int i = c1 - 1; i > c0; --i) {
+    const T v = (d[i * s] - (i < c1 - 1 ? G[i] * dn : T(0))) * IU[i];
+    d[i * s] = v;
+    dn = v;
+  }
+  d[c0 * s] = (T)phL;
+  if (l == a.p - 1) d[c1 * s] = (T)phR;
+}
+
+// Uploads the tables of axis slot k of shot s (built from the knots x, n[k] + 1 of them).
+static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<double>& x) {
+  NuHost t;
+  std::string why;
+  if (!nu_tables(x, s.p[k], s.d.n_nb, &t, &why)) return fail_msg(h, LOSS_E_ARG, why);
+  const size_t np = (size_t)s.n[k] + 1;
+  const size_t wbytes = t.W.size() * sizeof(double);
+  const size_t tbytes = 6 * np * s.esize;
+  std::vector<unsigned char> blob(wbytes + tbytes);
+  std::memcpy(blob.data(), t.W.data(), wbytes);
+  const std::vector<double>* cols[6] = {&t.A, &t.G, &t.L, &t.IU, &t.ra, &t.rb};
+  for (int c = 0; c < 6; ++c)
+    for (size_t i = 0; i < np; ++i) {
+      unsigned char* dst = blob.data() + wbytes + (c * np + i) * s.esize;
+      if (s.esize == 8) {
+        const double v = (*cols[c])[i];
+        std::memcpy(dst, &v, 8);
+      } else {
+        const float v = (float)(*cols[c])[i];
+        std::memcpy(dst, &v, 4);
+      }
+    }
+  if (s.nu_tab[k]) dev_free(h, s.nu_tab[k]);
+  s.nu_tab[k] = nullptr;
+  NU_TRY(dev_alloc(h, blob.size(), &s.nu_tab[k]));
+  NU_TRY(cuda_check(h, cudaMemcpyAsync(s.nu_tab[k], blob.data(), blob.size(), cudaMemcpyHostToDevice, h->stream),
+                      "upload knot tables"));
+  return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+}
+
+template <typename T>
+loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi) {
+  NuArgs<T> a{};
+  a.f = f;
+  a.d1 = d1;
+  a.phi = phi;
+  a.W = (const double*)s.nu_tab[k];
+  const size_t wl = 2 * (size_t)s.d.n_nb + 1;
+  a.tab = (const T*)((const unsigned char*)s.nu_tab[k] + (s.p[k] + 1) * wl * sizeof(double));
+  a.n = (int)s.n[k];
+  a.p = s.p[k];
+  a.M = a.n / a.p;
+  a.n_nb = s.d.n_nb;
+  const int64_t nx = s.len[2], ny = s.len[1], nz = s.len[0];
+  a.lines = s.dense / s.len[k];
+  if (k == 2) {  // x lines: q = (z, y) row index
+    a.stride = 1, a.inner = 1, a.inner_mul = 0, a.outer_stride = nx;
+  } else if (k == 1) {  // y lines: q = z * nx + x
+    a.stride = nx, a.inner = nx, a.inner_mul = 1, a.outer_stride = nx * ny;
+  } else {  // z lines: q = y * nx + x
+    a.stride = nx * ny, a.inner = 1, a.inner_mul = 0, a.outer_stride = 1;
+    (void)nz;
+  }
+  const int64_t threads = a.lines * a.p;
+  LaunchScope ls(h, LOSS_KERNEL_DERIVATIVE);
+  k_nu_deriv<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
+  return cuda_check(h, cudaGetLastError(), "non-uniform derivative kernel");
+}
+
+template loss_status_t run_nu_derivative<float>(loss_ctx*, Shot&, int, const float*, float*, double*);
+template loss_status_t run_nu_derivative<double>(loss_ctx*, Shot&, int, const double*, double*, double*);
+
+loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x) {
+  if (!x) {
+    if (s.nu_tab[k]) dev_free(h, s.nu_tab[k]);
+    s.nu_tab[k] = nullptr;
+    return LOSS_OK;
+  }
+  std::vector<double> xs(x, x + s.n[k] + 1);
+  return nu_upload(h, s, k, xs);
+}
+
+}  // namespace lossk

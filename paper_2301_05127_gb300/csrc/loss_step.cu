@@ -210,7 +210,7 @@ static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double 
     const unsigned mm = (unsigned)((((uint64_t)1 << 32) + (uint64_t)t.M - 1) / (uint64_t)t.M);
     const AcXArgs<float> a = ac_x_args<float>(h, s, LineGeom{}, do_B, acoef, amp);
     LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
-    return cuda_check(h, launch_xp<K>(a, t, mm, h->dflag, h->num_sms, h->stream), "acoustic x kernel");
+    return cuda_check(h, launch_xp<K>(a, t, mm, h->dflag, h->wait_polls, h->num_sms, h->stream), "acoustic x kernel");
   }
   return ac_x<float, K>(h, s, do_B, acoef, amp);
 }
@@ -387,6 +387,7 @@ static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A,
   for (int i = 0; i < 25; ++i) a.srcp.g[i] = s.src_g[i];
   a.src_explosive = (s.src_kinds & LOSS_SRC_EXPLOSIVE) ? 1 : 0;
   a.src_shear = (s.src_kinds & LOSS_SRC_SHEAR_XZ) ? 1 : 0;
+  a.force_mask = force_components(s.src_kinds);
   LaunchScope ls(h, kid);
   return cuda_check(h, launch_el<T, K>(a, pass, logc, threads, h->stream), "elastic kernel");
 }
@@ -395,7 +396,7 @@ static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A,
 template <typename T, bool K>
 static loss_status_t elastic_A(loss_ctx* h, Shot& s, double tau, double force_t) {
   double famp = 0.0;
-  if (s.src_on && (s.src_kinds & LOSS_SRC_FORCE_Z)) famp = tau * s.src_norm * ricker(force_t, s.src_f0, s.src_t0);
+  if (s.src_on && (s.src_kinds & kForceMask)) famp = tau * s.src_norm * ricker(force_t, s.src_f0, s.src_t0);
   LOSS_TRY((el_pass<T, K>(h, s, EL_BZ, 0, 1, tau, 0.0)));
   LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, tau, 0.0)));
   return el_pass<T, K>(h, s, EL_AY, 0, 1, tau, famp);
@@ -415,7 +416,7 @@ static loss_status_t elastic3d_step(loss_ctx* h, Shot& s) {
   if (s.src_on && (s.src_kinds & (LOSS_SRC_EXPLOSIVE | LOSS_SRC_SHEAR_XZ)))
     amp = dt * s.src_norm * ricker(tn + 0.5 * dt, s.src_f0, s.src_t0);
   double famp = 0.0;
-  if (s.src_on && (s.src_kinds & LOSS_SRC_FORCE_Z)) famp = dt * s.src_norm * ricker(tn + dt, s.src_f0, s.src_t0);
+  if (s.src_on && (s.src_kinds & kForceMask)) famp = dt * s.src_norm * ricker(tn + dt, s.src_f0, s.src_t0);
   LOSS_TRY((el_pass<T, K>(h, s, EL_BX, 1, 0, dt, 0.0)));
   LOSS_TRY((el_pass<T, K>(h, s, EL_BY, 1, 0, dt, 0.0)));
   LOSS_TRY((el_pass<T, K>(h, s, EL_BZ, 1, 1, dt, amp)));
@@ -565,7 +566,7 @@ static loss_status_t batch_launch_step(loss_ctx* h) {
       {
         LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
         LOSS_TRY(cuda_check(h, launch_xp_batch<K>((const XpShot*)B.xptab, unit0, bunit, bshot, B.xl, B.xpthreads,
-                                                  B.xpgrid, h->dflag, h->stream),
+                                                  B.xpgrid, h->dflag, h->wait_polls, h->stream),
                             "batched acoustic x kernel"));
       }
       for (int mode = 1; mode <= 2; ++mode) {
@@ -890,7 +891,7 @@ static loss_status_t step_batched_t(loss_ctx* h, int64_t n) {
                                       (int64_t)(intptr_t)B.xptab, (int64_t)(intptr_t)B.tztab, B.xpgrid, B.xpthreads,
                                       B.xl.total, B.tzthreads[0], B.tzthreads[1], B.tzlogc[0], B.tzlogc[1],
                                       B.tztiles, B.tzgrid[0], B.tzgrid[1],
-                                      (int64_t)B.tzsmem[0], (int64_t)B.tzsmem[1]};
+                                      (int64_t)B.tzsmem[0], (int64_t)B.tzsmem[1], (int64_t)h->wait_polls};
     if (!B.gexec || sig != B.gsig) {
       LOSS_TRY((capture_graph<T, K>(h, k)));
       B.gsig = sig;

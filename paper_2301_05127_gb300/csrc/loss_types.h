@@ -204,6 +204,7 @@ struct ElArgs {
   T* dlt[3];  // receiver corrections of the three velocity terms of this pass (in its layers), or null
   SourceArgs srcp;
   int src_explosive, src_shear;
+  int force_mask;  // body-force components of the source in the A passes: bit i = f_{i+1} (on v_{i+1})
 };
 
 // One term of the adjoint of the time step (see loss_kernels_adjoint.cu).  A term is a forward update

@@ -37,7 +37,7 @@ class Workload:
     steps: int
     model_fn: Callable[[], Tuple[np.ndarray, Optional[np.ndarray], np.ndarray]]
     src_index: Tuple[int, ...]
-    src_kinds: Tuple[str, ...]  # subset of "pressure", "explosive", "shear_xz", "force_z"
+    src_kinds: Tuple[str, ...]  # subset of "pressure", "explosive", "shear_xz", "force_x", "force_y", "force_z"
     f0: float  # Ricker peak frequency [Hz]
     t0: float  # Ricker delay [s]
     amp: float = 1.0
@@ -220,8 +220,8 @@ def elastic3d_double_layer(n: int = 128, nz: Optional[int] = None, p: int = 4, p
     gives the paper's z-refined grid), dt = 5 ms as printed.  The interface z = 0 lies on a grid point when nz is
     even and belongs to the upper layer.  The source sits at (0, 0, 10 km) with a Ricker history; the printed 100 Hz
     cannot be resolved at these spacings (a garbled unit), so f0 is a parameter, 0.5 Hz by default, with
-    t0 = 1.2 / f0.  The library's body force acts along z only, so the source is a z force.  Receivers: v3 on
-    the vertical line x = y = 0, where the paper samples v3(0, 0, z)."""
+    t0 = 1.2 / f0.  The source is the paper's body force along all three axes (f_1 = f_2 = f_3).  Receivers: v3
+    on the vertical line x = y = 0, where the paper samples v3(0, 0, z)."""
     nz = n if nz is None else nz
     pz = p if pz is None else pz
     shape = (nz + 1, n + 1, n + 1)
@@ -236,7 +236,8 @@ def elastic3d_double_layer(n: int = 128, nz: Optional[int] = None, p: int = 4, p
     line = np.arange(nz + 1, dtype=np.int64) * (n + 1) * (n + 1) + (n // 2) * (n + 1) + n // 2
     return Workload(
         name=f"elastic3d_double_layer_{nz}x{n}x{n}", dim=3, physics="elastic", n=(nz, n, n), p=(pz, p, p),
-        h=(hz, hxy, hxy), n_nb=n_nb, dt=0.005, steps=steps, model_fn=model, src_index=src, src_kinds=("force_z",),
+        h=(hz, hxy, hxy), n_nb=n_nb, dt=0.005, steps=steps, model_fn=model, src_index=src,
+        src_kinds=("force_x", "force_y", "force_z"),
         f0=f0, t0=1.2 / f0, receivers={"v3": line}, precision=precision, pml_width=pml_width)
 
 

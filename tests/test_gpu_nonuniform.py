@@ -1,0 +1,126 @@
+"""GPU parity of the LOSS derivative on non-uniform grids (loss_set_coordinates; the paper's Sec. 3 remark and its
+conclusion) against the oracle's B-spline collocation on the same knots (oracle/nonuniform.py), element by
+element: first derivatives and PMBC junction values, 2-D and 3-D, FP64 and FP32, several axes and patch counts."""
+import numpy as np
+import pytest
+
+from oracle import nonuniform as nu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as ge
+
+    ge.build()
+    import paper_2301_05127_gb300 as p
+
+    return p
+
+
+def _knots(n, seed, ratio=2.0, scale=10.0):
+    rng = np.random.default_rng(seed)
+    h = np.exp(rng.uniform(0.0, np.log(ratio), size=n)) * scale
+    return np.concatenate([[0.0], np.cumsum(h)])
+
+
+CASES = [
+    # dim, n, p, n_nb, non-uniform axes
+    (2, (64, 96), (2, 3), 12, (0, 1)),
+    (2, (120, 48), (4, 2), 10, (1,)),
+    (3, (24, 32, 40), (2, 2, 4), 8, (0, 1, 2)),
+    (3, (48, 36, 30), (3, 2, 1), 12, (1,)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonuniform_derivative_and_phi_match_oracle(pkg, case, prec):
+    dim, n, p, n_nb, axes = case
+    d = pkg.make_desc(dim, pkg.LOSS_ACOUSTIC, pkg.PRECISIONS[prec], n_nb, n, p, (10.0,) * dim, 1e-3)
+    g = pkg.Grid([d])
+    knots = {}
+    for a in axes:
+        knots[a] = _knots(n[a], 100 + a)
+        g.set_coordinates(0, a, knots[a])
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal(g.shape()).astype(g.dtype)
+    for a in range(dim):
+        x = knots.get(a, 10.0 * np.arange(n[a] + 1))
+        ref = nu.derivative(f.astype(np.float64), a, x, p[a], n_nb)
+        got = g.derivative(0, a, f).astype(np.float64)
+        assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max(), (a, prec)
+        if a in knots:
+            fm = np.moveaxis(f.astype(np.float64), a, -1).reshape(-1, n[a] + 1)
+            ref_phi = nu.pmbc_phi(fm, x, p[a], n_nb)
+            got_phi = g.pmbc_phi(0, a, f)
+            assert np.abs(got_phi - ref_phi).max() <= TOL[prec] * np.abs(ref_phi).max(), (a, prec)
+    g.close()
+
+
+def test_uniform_knots_equal_the_uniform_path(pkg):
+    """Knots with equal spacing through the non-uniform kernel give the uniform LOSS derivative (to rounding)."""
+    n, p, n_nb, h = (40, 56), (2, 4), 10, (2.5, 4.0)
+    d = pkg.make_desc(2, pkg.LOSS_ACOUSTIC, pkg.LOSS_FP64, n_nb, n, p, h, 1e-3)
+    a, b = pkg.Grid([d]), pkg.Grid([d])
+    for ax in range(2):
+        b.set_coordinates(0, ax, h[ax] * np.arange(n[ax] + 1) + 3.0)
+    f = np.random.default_rng(3).standard_normal(a.shape())
+    for ax in range(2):
+        ra, rb = a.derivative(0, ax, f), b.derivative(0, ax, f)
+        assert np.abs(ra - rb).max() < 1e-12 * np.abs(ra).max()
+    b.set_coordinates(0, 1, None)  # back to uniform spacing
+    assert np.array_equal(a.derivative(0, 1, f), b.derivative(0, 1, f))
+    a.close()
+    b.close()
+
+
+def test_nonuniform_rejections(pkg):
+    d = pkg.make_desc(2, pkg.LOSS_ACOUSTIC, pkg.LOSS_FP64, 8, (32, 32), (2, 2), (1.0, 1.0), 1e-3)
+    g = pkg.Grid([d])
+    bad = np.arange(33, dtype=np.float64)
+    bad[5] = bad[4]
+    with pytest.raises(pkg.LossError) as e:
+        g.set_coordinates(0, 0, bad)
+    assert e.value.status == pkg.LOSS_E_ARG
+    g.set_coordinates(0, 0, _knots(32, 1))
+    f = np.zeros(g.shape())
+    with pytest.raises(pkg.LossError) as e:
+        g.derivative(0, 0, f, second=True)
+    assert e.value.status == pkg.LOSS_E_UNSUPPORTED
+    g.set_model(0, np.full(g.shape(), 2000.0), None, np.full(g.shape(), 1000.0))
+    with pytest.raises(pkg.LossError) as e:
+        g.step(1)
+    assert e.value.status == pkg.LOSS_E_UNSUPPORTED
+    g.close()
+
+
+def test_nonuniform_derivative_throughput(pkg):
+    """257^3 FP32, 4 x 4 x 4 patches, n_nb = 20, non-uniform knots on every axis: one derivative per axis on device
+    arrays, timed with CUDA events after a warm-up (reported, and a floor against a pathological slowdown)."""
+    import torch
+
+    n = 256
+    d = pkg.make_desc(3, pkg.LOSS_ACOUSTIC, pkg.LOSS_FP32, 20, (n,) * 3, (4,) * 3, (10.0,) * 3, 1e-3)
+    g = pkg.Grid([d])
+    for a in range(3):
+        g.set_coordinates(0, a, _knots(n, 200 + a))
+    f = torch.randn((n + 1,) * 3, device="cuda", dtype=torch.float32)
+    res = {}
+    for a in range(3):
+        g.derivative(0, a, f)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            g.derivative(0, a, f)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        res[a] = ((n + 1) ** 3 / (ms * 1e-3), 8 * (n + 1) ** 3 / (ms * 1e-3) / 1e9)
+    print("non-uniform derivative 257^3 FP32, pt/s and GB/s (read f + write d) per axis z, y, x:", res)
+    assert min(v[0] for v in res.values()) > 1e9
+    g.close()

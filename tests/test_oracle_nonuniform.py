@@ -1,0 +1,88 @@
+"""Pins of the oracle's non-uniform-grid LOSS derivative (oracle/nonuniform.py; the paper's Sec. 3 remark that the
+construction carries over to non-uniform grids)."""
+import numpy as np
+import pytest
+from scipy.interpolate import CubicSpline
+
+from oracle import nonuniform as nu
+from oracle import spline
+
+
+def _knots(N, seed, ratio=2.0):
+    """Strictly increasing knots with neighbouring spacings within a factor `ratio` of each other overall."""
+    rng = np.random.default_rng(seed)
+    h = np.exp(rng.uniform(0.0, np.log(ratio), size=N))
+    return np.concatenate([[0.0], np.cumsum(h)]) * 7.0
+
+
+@pytest.mark.parametrize("N,p,seed", [(48, 4, 1), (36, 3, 2), (40, 1, 3)])
+def test_complete_sums_equal_natural_cubic_spline(N, p, seed):
+    """With n_nb >= N every PMBC sum is complete, so the patched derivative is the global natural spline's: it
+    must equal an independent natural cubic spline (scipy CubicSpline) at every knot, first and second
+    derivative."""
+    x = _knots(N, seed)
+    f = np.random.default_rng(seed + 10).standard_normal((3, N + 1))
+    d1, d2 = nu.derivative_1d(f, x, p, N, second=True)
+    for r in range(3):
+        cs = CubicSpline(x, f[r], bc_type="natural")
+        scale1 = np.abs(cs(x, 1)).max()
+        scale2 = np.abs(cs(x, 2)).max()
+        assert np.abs(d1[r] - cs(x, 1)).max() < 1e-11 * scale1
+        assert np.abs(d2[r] - cs(x, 2)).max() < 1e-10 * scale2
+
+
+@pytest.mark.parametrize("n,p,n_nb", [(32, 2, 6), (48, 4, 12)])
+def test_uniform_knots_reduce_to_the_uniform_oracle(n, p, n_nb):
+    """On equally spaced knots the B-splines are the paper's (rows (1, 4, 1)/6, derivative +-1/(2h)): the result
+    equals the uniform-grid oracle with the same truncated sums."""
+    h = 2.5
+    x = h * np.arange(n + 1)
+    f = np.random.default_rng(5).standard_normal((4, n + 1))
+    a1, a2 = nu.derivative_1d(f, x, p, n_nb, second=True)
+    b1, b2 = spline.derivative_1d(f, n, p, h, n_nb, second=True)
+    assert np.abs(a1 - b1).max() < 1e-12 * np.abs(b1).max()
+    assert np.abs(a2 - b2).max() < 1e-11 * np.abs(b2).max()
+
+
+def test_truncation_error_decays_exponentially():
+    """The weights of the global inverse decay geometrically away from the junction, so the error of the truncated
+    PMBC sums falls geometrically with n_nb (rate near |sqrt(3) - 2| = 0.268 for mild spacing variations)."""
+    N, p = 96, 4
+    x = _knots(N, 7, ratio=1.5)
+    f = np.random.default_rng(8).standard_normal((2, N + 1))
+    full = nu.derivative_1d(f, x, p, N)
+    errs = [np.abs(nu.derivative_1d(f, x, p, k) - full).max() for k in (4, 8, 12, 16)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a * 0.06  # four more terms: at most 0.06 of the error (0.268^4 = 5.2e-3 for uniform knots)
+    assert errs[-1] < 1e-8 * np.abs(full).max()
+
+
+def test_slope_equations_hold_inside_every_patch():
+    """C^2 continuity of the local spline at an interior knot i of a patch gives, whatever the junction values,
+    h_i d_{i-1} + 2 (h_{i-1} + h_i) d_i + h_{i-1} d_{i+1} = 3 (h_i (f_i - f_{i-1}) / h_{i-1}
+    + h_{i-1} (f_{i+1} - f_i) / h_i), with h_i = x_{i+1} - x_i (the non-uniform form of the compact identity)."""
+    N, p, n_nb = 60, 3, 5
+    x = _knots(N, 9)
+    f = np.random.default_rng(10).standard_normal((2, N + 1))
+    d = nu.derivative_1d(f, x, p, n_nb)
+    h = np.diff(x)
+    M = N // p
+    for l in range(p):
+        for i in range(l * M + 1, (l + 1) * M):
+            lhs = h[i] * d[:, i - 1] + 2 * (h[i - 1] + h[i]) * d[:, i] + h[i - 1] * d[:, i + 1]
+            rhs = 3 * (h[i] * (f[:, i] - f[:, i - 1]) / h[i - 1] + h[i - 1] * (f[:, i + 1] - f[:, i]) / h[i])
+            assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max() + 1e-13
+
+
+def test_junction_values_equal_phi_and_linear_fields_are_exact():
+    N, p, n_nb = 48, 4, 8
+    x = _knots(N, 11)
+    f = np.random.default_rng(12).standard_normal((3, N + 1))
+    d = nu.derivative_1d(f, x, p, n_nb)
+    phi = nu.pmbc_phi(f, x, p, n_nb)
+    M = N // p
+    for j in range(p + 1):
+        assert np.abs(d[:, j * M] - phi[:, j]).max() < 1e-12 * np.abs(phi).max()
+    lin = 3.0 - 0.7 * x  # with complete sums the natural spline reproduces linear data exactly
+    d_lin = nu.derivative_1d(lin[None, :], x, p, N)
+    assert np.abs(d_lin + 0.7).max() < 1e-12

@@ -70,7 +70,7 @@ def test_injected_pressure_is_conserved_before_the_waves_reach_the_ends():
     assert abs(total - injected) < 1e-9 * abs(injected), (total, injected)
 
 
-@pytest.mark.parametrize("kind", ["explosive", "shear_xz", "force_z"])
+@pytest.mark.parametrize("kind", ["explosive", "shear_xz", "force_x", "force_y", "force_z"])
 def test_elastic_sources_inject_exactly_their_own_components(kind):
     w = elastic3d_homogeneous(n=40, p=2, n_nb=8, steps=0, pml_width=0)
     # 60 Hz: stop at 0.016 s, near the extremum of the running integral; the field reaches about 11 cells from
@@ -91,8 +91,26 @@ def test_elastic_sources_inject_exactly_their_own_components(kind):
     elif kind == "shear_xz":
         expect["s13"] = stress_in
     else:
-        expect["v3"] = impulse
+        expect["v" + {"x": "1", "y": "2", "z": "3"}[kind[-1]]] = impulse
     scale = max(abs(v) for v in expect.values())
     assert scale > 1e-4
     for f in sums:
         assert abs(sums[f] - expect[f]) < 1e-8 * scale, (f, sums[f], expect[f])
+
+
+@pytest.mark.parametrize("kind,axis", [("force_x", 2), ("force_y", 1)])
+def test_body_force_axes_follow_the_grid_axes(kind, axis):
+    """On a cubic homogeneous grid a body force along x (y) radiates the field of the force along z with the grid
+    axes z and x (y) exchanged: v_x from force_x is v_z from force_z transposed, and so on for every component.
+    Together with the Stokes pin of the z force this pins the direction and sign of the other two."""
+    w = elastic3d_homogeneous(n=24, p=2, n_nb=8, steps=0, pml_width=4)
+    w = dataclasses.replace(w, receivers={}, f0=60.0, t0=1.2 / 60.0)
+    ref = Simulation(dataclasses.replace(w, src_kinds=("force_z",))).step(10, record=False).state
+    got = Simulation(dataclasses.replace(w, src_kinds=(kind,))).step(10, record=False).state
+    comp = {2: "1", 1: "2"}[axis]  # the velocity component along the exchanged axis
+    swap = {"v3": "v" + comp, "v" + comp: "v3"}
+    scale = max(float(np.abs(v).max()) for v in ref.values())
+    assert scale > 0
+    for f in ("v1", "v2", "v3"):
+        expect = np.swapaxes(ref[swap.get(f, f)], 0, axis)
+        assert np.abs(got[f] - expect).max() < 1e-12 * scale, f
