@@ -419,6 +419,29 @@ static loss_status_t copy_in(loss_ctx* h, const Shot& s, void* dst, const void* 
                     "copy in");
 }
 
+// Host upload of a field: a pinned host array goes through one 1-D copy into a dense device staging buffer and
+// the pitch kernel (faster than a 2-D copy from host memory); pageable arrays take the 2-D copy.
+static loss_status_t upload_field(loss_ctx* h, const Shot& s, void* dst, const void* src, int mem) {
+  if (mem != LOSS_MEM_HOST) return copy_in(h, s, dst, src, mem);
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+    cudaGetLastError();
+    return copy_in(h, s, dst, src, mem);
+  }
+  if (at.type != cudaMemoryTypeHost) return copy_in(h, s, dst, src, mem);
+  const size_t bytes = (size_t)s.dense * s.esize;
+  if (h->stage_bytes < bytes) {
+    if (h->stage) dev_free(h, h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    LOSS_TRY(dev_alloc(h, bytes, &h->stage));
+    h->stage_bytes = bytes;
+  }
+  LOSS_TRY(cuda_check(h, cudaMemcpyAsync(h->stage, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in"));
+  return cuda_check(h, launch_pitch_in(h->stage, dst, s.len[0] * s.len[1], s.len[2], s.px, s.esize, h->num_sms,
+                                       h->stream), "pitch kernel");
+}
+
 static loss_status_t copy_out(loss_ctx* h, const Shot& s, void* dst, const void* src, int mem) {
   const size_t w = (size_t)s.len[2] * s.esize;
   return cuda_check(h, cudaMemcpy2DAsync(dst, w, src, (size_t)s.px * s.esize, w, (size_t)(s.len[0] * s.len[1]),
@@ -980,7 +1003,7 @@ loss_status_t loss_set_field(loss_handle_t h, int32_t shot, int32_t field, const
   if (!field_used(*s, field)) return fail(h, LOSS_E_ARG, "field not present on this grid");
   if (!src || (mem != LOSS_MEM_HOST && mem != LOSS_MEM_DEVICE)) return fail(h, LOSS_E_ARG, "bad source buffer");
   LOSS_TRY(unstagger(h, *s));
-  LOSS_TRY(copy_in(h, *s, s->field[field], src, mem));
+  LOSS_TRY(upload_field(h, *s, s->field[field], src, mem));
   if (s->kahan)
     LOSS_TRY(cuda_check(h, cudaMemsetAsync(s->comp[field], 0, (size_t)s->total * s->esize, h->stream), "memset"));
   if (mem == LOSS_MEM_HOST) LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));

@@ -146,6 +146,8 @@ struct loss_ctx {
   // 1 + shot * LOSS_NUM_FIELDS + field of the first non-finite field found (read and cleared by loss_sync)
   int64_t watch_every = 0, watch_count = 0;
   int* nflag = nullptr;
+  void* stage = nullptr;  // dense device staging buffer of pinned host uploads (loss_set_field)
+  size_t stage_bytes = 0;
   int graph_steps = 0;   // > 0: steps are replayed from a captured CUDA graph of this many steps
   bool capturing = false;
   lossk::BatchState batch;
@@ -240,6 +242,9 @@ cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshot
 template <typename T>
 cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
 cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
+// loss_copy.cu: dst[r * pitch + c] = src[r * cols + c] on the device
+cudaError_t launch_pitch_in(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,
+                            int num_sms, cudaStream_t st);
 // loss_watch.cu: sets *flag to code (if it is still 0) when one of the n values at f is not finite
 cudaError_t launch_finite(const void* f, int64_t n, size_t esize, int* flag, int code, int num_sms, cudaStream_t st);
 template <bool KAHAN>

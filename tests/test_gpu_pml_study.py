@@ -6,8 +6,7 @@ with the absorbing layer in the padding.  At every 200 steps up to t = 0.2 s, th
 the domain is taken against the free-space solution of the time stepping and compared with the oracle's value.
 The FP64 path follows the oracle to rounding, so the two agree to far better than the 1e-4 allowed here.
 
-About a minute of host work (the free-space solutions) plus 14 runs of 2000 steps.  It runs only when
-LOSS_GPU_STUDIES=1 is set, because it has not yet run on a GPU; the default GPU suite stays as verified.
+About a minute of host work (the free-space solutions) plus 14 runs of 2000 steps.
 """
 import collections
 import dataclasses
@@ -19,9 +18,7 @@ import pytest
 from oracle.exact import pulse_on_grid
 from synth import gaussian_pulse_2d
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("LOSS_GPU_STUDIES") != "1",
-                                 reason="set LOSS_GPU_STUDIES=1 to run the PML study on the GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
