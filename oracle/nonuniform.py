@@ -178,3 +178,39 @@ def derivative(f: np.ndarray, axis: int, x: np.ndarray, p: int, n_nb: int, secon
     if second:
         return tuple(np.moveaxis(o.reshape(shp), -1, axis) for o in out)
     return np.moveaxis(out.reshape(shp), -1, axis)
+
+
+class Operator:
+    """Per-axis LOSS first derivative on a tensor grid whose axes may carry their own knots (the interface of
+    ``wave.Operator``): axis a uses the knots ``knots[a]`` when given, else the uniform spacing h[a]."""
+
+    def __init__(self, n, p, h, n_nb, knots):
+        from . import spline
+
+        self._spline = spline
+        self.n, self.p, self.h, self.n_nb = tuple(n), tuple(p), tuple(h), int(n_nb)
+        self.dim = len(self.n)
+        self.knots = {int(a): np.asarray(x, dtype=np.float64) for a, x in knots.items()}
+
+    def D(self, f: np.ndarray, axis: int) -> np.ndarray:
+        if axis in self.knots:
+            return derivative(f, axis, self.knots[axis], self.p[axis], self.n_nb)
+        return self._spline.derivative(f, axis, self.n[axis], self.p[axis], self.h[axis], self.n_nb)
+
+    def Dc(self, f: np.ndarray, comp: int) -> np.ndarray:
+        from .wave import component_axis
+
+        return self.D(f, component_axis(comp, self.dim))
+
+
+def simulation(w, knots, state=None):
+    """A ``wave.Simulation`` of workload w whose derivatives use the given knots (dict axis -> coordinates).  The
+    time stepping is the literal Strang sequence of ``wave``; absorbing layers and point sources, whose profiles
+    are defined on the uniform spacing, are not supported on such grids."""
+    from .wave import Simulation
+
+    if getattr(w, "pml_width", 0) or w.src_kinds:
+        raise ValueError("non-uniform grids: no absorbing layer and no point source")
+    sim = Simulation(w, state=state)
+    sim.op = Operator(w.n, w.p, w.h, w.n_nb, knots)
+    return sim

@@ -1035,8 +1035,6 @@ loss_status_t loss_step(loss_handle_t h, int64_t n_steps) {
   for (Shot& s : h->shots) {
     if (!s.has_model) return fail(h, LOSS_E_STATE, "loss_set_model must be called for every shot before stepping");
   }
-  for (Shot& s : h->shots)
-    if (any_nonuniform(s)) return fail(h, LOSS_E_UNSUPPORTED, "time steps on non-uniform grids are not built");
   for (Shot& s : h->shots) LOSS_TRY(ensure_trace_capacity(h, s, s.rcv_steps + n_steps));
   if (batch_eligible(h)) {
     LOSS_TRY(step_batched(h, n_steps));
@@ -1091,6 +1089,7 @@ loss_status_t loss_set_coordinates(loss_handle_t h, int32_t shot, int32_t axis, 
   Shot* s;
   LOSS_TRY(get_shot(h, shot, &s));
   if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
+  LOSS_TRY(unstagger(h, *s));  // the fields go back to the integer time level before the operator changes
   return set_coordinates(h, *s, axis_slot(*s, axis), x);
 }
 

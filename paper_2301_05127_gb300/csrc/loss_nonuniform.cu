@@ -24,12 +24,14 @@
 // lines along y and z (consecutive x) load and store coalesced; lines along x are walked by each thread alone.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "loss_host.h"
+#include "loss_line.cuh"
 
 namespace lossk {
 
@@ -222,8 +224,11 @@ static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<do
   return cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
 }
 
+// Derivative along axis slot k of a field stored with row pitch py (elements between consecutive y, or z in 2-D,
+// rows) and plane pitch pz: dense arrays have py = nx, pz = nx * ny; the handle's fields have py = s.sy, pz = s.sz.
 template <typename T>
-loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi) {
+static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, int64_t py, int64_t pz,
+                               int kernel) {
   NuArgs<T> a{};
   a.f = f;
   a.d1 = d1;
@@ -235,20 +240,107 @@ loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, 
   a.p = s.p[k];
   a.M = a.n / a.p;
   a.n_nb = s.d.n_nb;
-  const int64_t nx = s.len[2], ny = s.len[1], nz = s.len[0];
+  const int64_t nx = s.len[2], ny = s.len[1];
   a.lines = s.dense / s.len[k];
-  if (k == 2) {  // x lines: q = (z, y) row index
-    a.stride = 1, a.inner = 1, a.inner_mul = 0, a.outer_stride = nx;
+  if (k == 2) {  // x lines: q = z * ny + y
+    a.stride = 1, a.inner = ny, a.inner_mul = py, a.outer_stride = pz;
   } else if (k == 1) {  // y lines: q = z * nx + x
-    a.stride = nx, a.inner = nx, a.inner_mul = 1, a.outer_stride = nx * ny;
+    a.stride = py, a.inner = nx, a.inner_mul = 1, a.outer_stride = pz;
   } else {  // z lines: q = y * nx + x
-    a.stride = nx * ny, a.inner = 1, a.inner_mul = 0, a.outer_stride = 1;
-    (void)nz;
+    a.stride = pz, a.inner = nx, a.inner_mul = 1, a.outer_stride = py;
   }
   const int64_t threads = a.lines * a.p;
-  LaunchScope ls(h, LOSS_KERNEL_DERIVATIVE);
+  LaunchScope ls(h, kernel);
   k_nu_deriv<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
   return cuda_check(h, cudaGetLastError(), "non-uniform derivative kernel");
+}
+
+template <typename T>
+loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi) {
+  return nu_launch<T>(h, s, k, f, d1, phi, s.len[2], s.len[2] * s.len[1], LOSS_KERNEL_DERIVATIVE);
+}
+
+// --- time step on grids with non-uniform axes (2-D acoustic) ------------------------------------------------
+// The literal Strang sequence of Sec. 3.3 (half A, B, half A) with every derivative taken on the axis's knots; the
+// velocities are kept at the integer time level (no staggering), so a step is six derivatives and three pointwise
+// updates.  Axes without knots of their own get equally spaced ones, so that every derivative uses one kernel.
+
+// u += coef * scale * (g0 + g1) (g1 may be null; coef an array or the scalar coef0), compensated when K.
+template <typename T, bool K>
+__global__ void __launch_bounds__(256) k_nu_update(T* __restrict__ u, T* __restrict__ c, const T* __restrict__ g0,
+                                                   const T* __restrict__ g1, const T* __restrict__ coef, T coef0,
+                                                   T scale, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const T g = g1 ? g0[i] + g1[i] : g0[i];
+    const T delta = (scale * (coef ? coef[i] : coef0)) * g;
+    if constexpr (K) {
+      float v = u[i], cc = c[i];
+      kahan_add(v, cc, delta);
+      u[i] = v;
+      c[i] = cc;
+    } else {
+      u[i] += delta;
+    }
+  }
+}
+
+loss_status_t nu_ensure_axes(loss_ctx* h, Shot& s) {
+  for (int k = 0; k < 3; ++k) {
+    if (s.dim == 2 && k == 1) continue;
+    if (s.nu_tab[k]) continue;
+    std::vector<double> x((size_t)s.n[k] + 1);
+    for (size_t i = 0; i < x.size(); ++i) x[i] = s.h[k] * (double)i;
+    NU_TRY(nu_upload(h, s, k, x));
+  }
+  if (!s.tmp[1]) {
+    NU_TRY(dev_alloc(h, (size_t)s.total * s.esize, &s.tmp[1]));
+    NU_TRY(cuda_check(h, cudaMemsetAsync(s.tmp[1], 0, (size_t)s.total * s.esize, h->stream), "memset"));
+  }
+  return LOSS_OK;
+}
+
+template <typename T, bool K>
+static loss_status_t nu_update(loss_ctx* h, Shot& s, int field, const void* g0, const void* g1, const void* coef,
+                               double coef0, double scale) {
+  const int grid = (int)std::min<int64_t>((s.total + 255) / 256, 8LL * h->num_sms);
+  LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X2);
+  k_nu_update<T, K><<<grid, 256, 0, h->stream>>>((T*)s.field[field], K ? (T*)s.comp[field] : nullptr,
+                                                  (const T*)g0, (const T*)g1, (const T*)coef, (T)coef0, (T)scale,
+                                                  s.total);
+  return cuda_check(h, cudaGetLastError(), "non-uniform update kernel");
+}
+
+template <typename T, bool K>
+static loss_status_t nu_step_t(loss_ctx* h, Shot& s) {
+  const double dt = s.d.dt;
+  T* t0 = (T*)s.tmp[0];
+  T* t1 = (T*)s.tmp[1];
+  const void* b = s.b_const ? nullptr : s.model[1];
+  auto half_A = [&]() -> loss_status_t {
+    NU_TRY(nu_launch<T>(h, s, 2, (const T*)s.field[LOSS_FIELD_SIGMA], t0, nullptr, s.sy, s.sz,
+                        LOSS_KERNEL_ACOUSTIC_X));
+    NU_TRY(nu_launch<T>(h, s, 0, (const T*)s.field[LOSS_FIELD_SIGMA], t1, nullptr, s.sy, s.sz,
+                        LOSS_KERNEL_ACOUSTIC_Z));
+    NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_V1, t0, nullptr, b, s.b0, -0.5 * dt)));
+    return nu_update<T, K>(h, s, LOSS_FIELD_V3, t1, nullptr, b, s.b0, -0.5 * dt);
+  };
+  NU_TRY(half_A());
+  NU_TRY(nu_launch<T>(h, s, 2, (const T*)s.field[LOSS_FIELD_V1], t0, nullptr, s.sy, s.sz, LOSS_KERNEL_ACOUSTIC_X));
+  NU_TRY(nu_launch<T>(h, s, 0, (const T*)s.field[LOSS_FIELD_V3], t1, nullptr, s.sy, s.sz, LOSS_KERNEL_ACOUSTIC_Z));
+  NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_SIGMA, t0, t1, s.model[0], 0.0, -dt)));
+  return half_A();
+}
+
+loss_status_t nu_step(loss_ctx* h, Shot& s) {
+  if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2)
+    return fail_msg(h, LOSS_E_UNSUPPORTED, "time steps on non-uniform grids are built for 2-D acoustic grids");
+  if (s.pml_on || s.src_on)
+    return fail_msg(h, LOSS_E_UNSUPPORTED, "non-uniform grids: no absorbing layer and no point source");
+  NU_TRY(nu_ensure_axes(h, s));
+  if (s.esize == 8) return nu_step_t<double, false>(h, s);
+  if (s.kahan) return nu_step_t<float, true>(h, s);
+  return nu_step_t<float, false>(h, s);
 }
 
 template loss_status_t run_nu_derivative<float>(loss_ctx*, Shot&, int, const float*, float*, double*);

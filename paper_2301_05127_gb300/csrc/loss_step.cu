@@ -448,7 +448,9 @@ bool batch_eligible(const loss_ctx* h) {
   if (!(h->graph_steps > 0 || (h->batched && h->shots.size() > 1))) return false;
   const Shot& s0 = h->shots[0];
   for (const Shot& s : h->shots)
-    if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2 || s.esize != s0.esize || s.kahan != s0.kahan) return false;
+    if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2 || s.esize != s0.esize || s.kahan != s0.kahan ||
+        any_nonuniform(s))
+      return false;
   return true;
 }
 
@@ -921,6 +923,20 @@ loss_status_t step_batched(loss_ctx* h, int64_t n) {
 }
 
 loss_status_t step_shot(loss_ctx* h, Shot& s) {
+  if (any_nonuniform(s)) {
+    LOSS_TRY(nu_step(h, s));
+    // receivers at the integer time level (the non-uniform step keeps no staggered velocities)
+    if (s.esize == 8) {
+      LOSS_TRY(gather_fields<double>(h, s, true, 0));
+      LOSS_TRY(gather_fields<double>(h, s, false, 0));
+    } else {
+      LOSS_TRY(gather_fields<float>(h, s, true, 0));
+      LOSS_TRY(gather_fields<float>(h, s, false, 0));
+    }
+    if (s.n_rcv) ++s.rcv_steps;
+    ++s.step;
+    return LOSS_OK;
+  }
   if (s.d.physics == LOSS_ACOUSTIC && s.dim == 2) {
     if (s.esize == 8) return acoustic2d_step<double, false>(h, s);
     if (s.kahan) return acoustic2d_step<float, true>(h, s);
