@@ -475,6 +475,7 @@ def run_ours(args):
                          / (ms_per_step * 1e-3) / 1e9 / peak,
                          "durations": "CUDA events around each launch in a second pass of K flushed steps"},
             "ms_per_step_with_launch_events": sum(prof_ms) / len(prof_ms),
+            "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
             "kernels_ms_per_launch": {k: (v[0] / max(v[1], 1)) for k, v in kern.items()},
             "kernels_frac_of_peak": {k: _alg_bytes_per_point(k, 4, True, False) * pts / (kern[k][0] / kern[k][1] * 1e-3)
                                      / (peak * 1e9) for k in KERNELS if kern[k][1]},

@@ -254,6 +254,10 @@ template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, unsigned polls,
                       int num_sms, cudaStream_t st);
 size_t tile_smem_z(const TileGeom& t, int mode, int logc);
+// loss_kernels_elastic.cu: elastic y / z tile passes (FP32)
+size_t elt_smem(const ElTile& g, int logc);
+template <bool KAHAN>
+cudaError_t launch_elt(const ElArgs<float>& a, const ElTile& g, int pass, int logc, cudaStream_t st);
 size_t xp_smem(const TileGeom& t, bool kahan);
 int xp_rows_per_unit(int n, int threads);
 XpSmem xp_batch_layout(const std::vector<TileGeom>& ts, const std::vector<int>& rs, bool kahan);

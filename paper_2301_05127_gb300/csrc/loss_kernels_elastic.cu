@@ -16,7 +16,9 @@
 
 #include "../../include/loss.h"
 #include "loss_block.cuh"
+#include "loss_fir.cuh"
 #include "loss_line.cuh"
+#include "loss_tile.cuh"
 #include "loss_types.h"
 
 namespace lossk {
@@ -242,6 +244,230 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
     });
   }
 }
+
+// ---------------------------------------------------------------------------------------------------------------
+// y and z passes of the FP32 step on one-patch tiles, in the truncated-convolution form of loss_fir.cuh (the 2-D z
+// tiles' arithmetic): a block takes 32 neighbouring x columns by one patch of the pass axis plus a halo of
+// H = max(n_nb, K) positions on each side, for one index of the remaining axis.  It stages the pass's three source
+// fields (128-byte row segments), forms the FP64 junction corrections of the patch's two junctions for each field,
+// computes the three derivatives of its chunk in registers and applies the pass's pointwise update:
+//   ET_BY (y):  TB += X[v1,y], TD = X[v2,y], TE = X[v3,y]
+//   ET_BZ (z):  the stress sub-step (as EL_BZ with do_B) from TA..TE and X[v1..v3, z], + source
+//   ET_AZ (z):  UA = Y[s13,z], UB = Y[s23,z], UC = Y[s33,z] (from the new stresses)
+//   ET_AY (y):  v_i += b (U_i + Y[s_i2, y]) (as EL_AY), + body force
+// Tiles are independent: no block holds a whole line.  The z part of the velocity sub-step is a pass of its own
+// (the line kernel computes it on the stresses BZ leaves on chip; a tile has no neighbour's new stresses).
+template <int PASS, bool KAHAN, int LOGC>
+__global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
+  constexpr int C = 1 << LOGC;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ float rpow[kFirPow];
+  __shared__ float dl[3][64];
+  __shared__ double jpart[16 * 32];
+  __shared__ double wsm[2 * 129];
+  const TileGeom& t = g.t;
+  const int l = blockIdx.x % t.p;
+  const int rest = blockIdx.x / t.p;
+  const int cg = rest % g.ncg;
+  const int outer = rest / g.ncg;
+  const int x0 = cg * 32;
+  const int z0 = l * t.M;  // the patch along the pass axis
+  const int zb = z0 - t.H;
+  const int rows = t.M + 2 * t.H + 1;
+  const int nch = (t.M + C - 1) / C;
+  const bool last = l == t.p - 1;
+  const int64_t obase = (int64_t)outer * g.ostride + x0;
+  float* F = reinterpret_cast<float*>(sm);  // three fields, [rows][32] each
+  float* PA = F + 3 * rows * 32;            // [chunk][32] warm-up partial sums
+  float* PB = PA + nch * 32;
+  fill_rpow(rpow, t.r);
+  {
+    const int wl = 2 * t.Rd + 1;
+    for (int i = threadIdx.x; i < 2 * wl; i += blockDim.x) wsm[i] = t.Wd[(size_t)l * wl + i];
+  }
+  for (int s = 0; s < 3; ++s) {
+    const float* f = a.src[s] + obase;
+    float* Fs = F + s * rows * 32;
+    for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
+      const int q = i >> 3, seg = i & 7;
+      const int pos = zb + q;
+      if (pos >= 0 && pos <= t.n) cp_async<16>(Fs + q * 32 + seg * 4, f + (int64_t)pos * t.px + seg * 4);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  const ZBun bun{zb};
+  const int nvalid = min(32, g.nx - x0);
+  const int nwj = blockDim.x >> 5;
+  for (int s = 0; s < 3; ++s) {
+    tile_junctions_z(F + s * rows * 32, bun, nvalid, l, t, nwj, wsm, jpart, dl[s]);
+    __syncthreads();
+  }
+  const int col = threadIdx.x & 31;
+  const int c = threadIdx.x >> 5;
+  const int p0 = z0 + c * C;
+  const int len = min(C, z0 + t.M - p0);
+  const int lenx = len + ((len > 0 && last && p0 + len == t.n) ? 1 : 0);  // with the line's last point
+  const bool mine = len > 0 && col < nvalid;
+  constexpr int W = FirLen<float>::K / C;
+  const float rC = rpow[C];
+  // each field's derivative of the chunk replaces the field's own rows in the tile once every warm-up read of
+  // them is done; a thread reads back only what it wrote
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    float* Fs = F + s * rows * 32;
+    float fv[C + 1], e[C + 1];
+    if (mine) {
+#pragma unroll
+      for (int j = 0; j <= C; ++j)
+        if (j < lenx) fv[j] = Fs[bun.at(col, p0 + j)];
+      if (len == C) chunk_partials<C>(fv, t.r, PA[c * 32 + col], PB[c * 32 + col]);
+    }
+    __syncthreads();
+    if (mine) {
+      float sL, qR;
+      if (c >= W) {
+        sL = PA[(c - 1) * 32 + col];
+        if (W == 2) sL += rC * PA[(c - 2) * 32 + col];
+      } else {
+        sL = fir_left<float, FirLen<float>::K>(Fs, bun, col, p0, t.n, t.r);
+      }
+      if (lenx == C && (c + W + 1) * C <= t.M) {
+        qR = PB[(c + 1) * 32 + col];
+        if (W == 2) qR += rC * PB[(c + 2) * 32 + col];
+      } else {
+        qR = fir_right<float, FirLen<float>::K>(Fs, bun, col, p0 + lenx - 1, t.n, t.r);
+      }
+      tile_chunk_e<C>(fv, p0, lenx, z0, t, dl[s] + 2 * col, rpow, sL, qR, e);
+    }
+    __syncthreads();
+    if (mine) {
+#pragma unroll
+      for (int j = 0; j <= C; ++j)
+        if (j < lenx) Fs[bun.at(col, p0 + j)] = e[j];
+    }
+  }
+  if (!mine) return;
+  const float dt = a.dt, ta = a.acoef, s3h = t.s3h;
+  float* const* tt = a.tmp;
+#pragma unroll
+  for (int j = 0; j <= C; ++j) {
+    if (j >= lenx) break;
+    const int pos = p0 + j;
+    const int64_t gi = obase + (int64_t)pos * t.px + col;
+    const int k = bun.at(col, pos);
+    const float g0 = s3h * F[k], g1 = s3h * F[rows * 32 + k], g2 = s3h * F[2 * rows * 32 + k];
+    if (PASS == ET_BY) {
+      const float t1 = tt[1][gi];
+      const float y0 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt);
+      const float y1 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt);
+      const float y2 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt);
+      tt[1][gi] = t1 + y0;
+      tt[3][gi] = y1;
+      tt[4][gi] = y2;
+    } else if (PASS == ET_BZ) {
+      // every global operand of the point first, then the arithmetic, then the stores
+      const int fs[6] = {LOSS_FIELD_S11, LOSS_FIELD_S22, LOSS_FIELD_S12, LOSS_FIELD_S13, LOSS_FIELD_S23,
+                         LOSS_FIELD_S33};
+      float u[6], cu[6];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        u[f] = a.fld[fs[f]][gi];
+        cu[f] = KAHAN ? a.cmp[fs[f]][gi] : 0.0f;
+      }
+      const float xa = tt[0][gi], xd = tt[3][gi], tc = tt[2][gi], tb = tt[1][gi], te = tt[4][gi];
+      const float lam = a.lam ? a.lam[gi] : a.lam0;
+      const float mu = a.mu ? a.mu[gi] : a.mu0;
+      const float x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt);  // v1 along z
+      const float x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt);  // v2 along z
+      const float x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt);  // v3 along z
+      const float ltr = lam * (xa + xd + x33);
+      float s11 = ltr + 2.0f * mu * xa, s22 = ltr + 2.0f * mu * xd, s33 = ltr + 2.0f * mu * x33;
+      float s13 = mu * (tc + x13);
+      if (a.srcp.on) {
+        const int dz = pos - a.srcp.zs + 12, dy = outer - a.srcp.ys + 12, dx = x0 + col - a.srcp.xs + 12;
+        if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u) {
+          const float sv = (float)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
+          if (a.src_explosive) s11 += sv, s22 += sv, s33 += sv;
+          if (a.src_shear) s13 += sv;
+        }
+      }
+      const float d[6] = {s11, s22, mu * tb, s13, mu * (te + x23), s33};
+#pragma unroll
+      for (int f = 0; f < 6; ++f) upd_r<float, KAHAN>(u[f], cu[f], d[f]);
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        a.fld[fs[f]][gi] = u[f];
+        if (KAHAN) a.cmp[fs[f]][gi] = cu[f];
+      }
+    } else if (PASS == ET_AZ) {
+      tt[5][gi] = effA(a, 0, gi, pos, g0, ta);
+      tt[6][gi] = effA(a, 1, gi, pos, g1, ta);
+      tt[7][gi] = effA(a, 2, gi, pos, g2, ta);
+    } else {  // ET_AY
+      const float b = a.b ? a.b[gi] : a.b0;
+      float force = 0.0f;  // body force (FORCE_X/Y/Z sources), already multiplied by the sub-step length
+      if (a.srcp.on) {
+        const int dz = outer - a.srcp.zs + 12, dy = pos - a.srcp.ys + 12, dx = x0 + col - a.srcp.xs + 12;
+        if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u)
+          force = (float)(a.srcp.amp * a.srcp.g[dz] * a.srcp.g[dy] * a.srcp.g[dx]);
+      }
+      const float f0 = (a.force_mask & 1) ? force : 0.0f, f1 = (a.force_mask & 2) ? force : 0.0f,
+                  f2 = (a.force_mask & 4) ? force : 0.0f;
+      float u[3], cu[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        u[f] = a.fld[LOSS_FIELD_V1 + f][gi];
+        cu[f] = KAHAN ? a.cmp[LOSS_FIELD_V1 + f][gi] : 0.0f;
+      }
+      const float t5 = tt[5][gi], t6 = tt[6][gi], t7 = tt[7][gi];
+      const float d0 = b * (t5 + effA(a, 0, gi, pos, g0, ta) + f0);
+      const float d1 = b * (t6 + effA(a, 1, gi, pos, g1, ta) + f1);
+      const float d2 = b * (t7 + effA(a, 2, gi, pos, g2, ta) + f2);
+      upd_r<float, KAHAN>(u[0], cu[0], d0);
+      upd_r<float, KAHAN>(u[1], cu[1], d1);
+      upd_r<float, KAHAN>(u[2], cu[2], d2);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        a.fld[LOSS_FIELD_V1 + f][gi] = u[f];
+        if (KAHAN) a.cmp[LOSS_FIELD_V1 + f][gi] = cu[f];
+      }
+    }
+  }
+}
+
+size_t elt_smem(const ElTile& g, int logc) {
+  const int rows = g.t.M + 2 * g.t.H + 1;
+  const int nch = (g.t.M + (1 << logc) - 1) >> logc;
+  return (size_t)3 * rows * 32 * 4 + (size_t)2 * nch * 32 * 4;
+}
+
+template <int PASS, bool KAHAN>
+static cudaError_t launch_elt_pass(const ElArgs<float>& a, const ElTile& g, int logc, cudaStream_t st) {
+  ElArgs<float> aa = a;
+  ElTile gg = g;
+  void* argv[] = {&aa, &gg};
+  const int threads = 32 * ((g.t.M + (1 << logc) - 1) >> logc);
+  const int grid = g.t.p * g.ncg * g.nouter;
+  const size_t smem = elt_smem(g, logc);
+  auto kern = logc == 3 ? k_elt<PASS, KAHAN, 3> : k_elt<PASS, KAHAN, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(threads), argv, smem, st);
+}
+
+template <bool KAHAN>
+cudaError_t launch_elt(const ElArgs<float>& a, const ElTile& g, int pass, int logc, cudaStream_t st) {
+  switch (pass) {
+    case ET_BY: return launch_elt_pass<ET_BY, KAHAN>(a, g, logc, st);
+    case ET_BZ: return launch_elt_pass<ET_BZ, KAHAN>(a, g, logc, st);
+    case ET_AZ: return launch_elt_pass<ET_AZ, KAHAN>(a, g, logc, st);
+    default: return launch_elt_pass<ET_AY, KAHAN>(a, g, logc, st);
+  }
+}
+template cudaError_t launch_elt<false>(const ElArgs<float>&, const ElTile&, int, int, cudaStream_t);
+template cudaError_t launch_elt<true>(const ElArgs<float>&, const ElTile&, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------------------------
 template <class K>

@@ -320,34 +320,17 @@ static loss_status_t acoustic2d_unstagger(loss_ctx* h, Shot& s) {
 // 3-D elastic: five line passes per step (loss_kernels_elastic.cu).
 enum { EL_BX = 0, EL_BY = 1, EL_BZ = 2, EL_AX = 3, EL_AY = 4 };
 
-template <typename T, bool K>
-static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A, double acoef, double amp) {
-  // internal axis slot of the pass: x = 2, y = 1, z = 0
-  const int k = (pass == EL_BX || pass == EL_AX) ? 2 : ((pass == EL_BY || pass == EL_AY) ? 1 : 0);
-  LineGeom g;
-  int logc, threads;
-  const int kid = (k == 2) ? LOSS_KERNEL_ELASTIC_X : (k == 1 ? LOSS_KERNEL_ELASTIC_Y : LOSS_KERNEL_ELASTIC_Z);
-  // Built-in FP32 shapes of the elastic passes (what the autotuner picks on the 257^3 and 193^3 grids): chunks of
-  // 8 unknowns on every axis, 128 threads per x block and 256 per y / z block.
-  int want_threads = h->tile_threads[kid], want_logc = h->chunk_log2[kid];
-  if (sizeof(T) == 4 && h->lines_per_block[kid] <= 0) {
-    if (want_threads <= 0) want_threads = k == 2 ? 128 : 256;
-    if (want_logc <= 0) want_logc = 3;
-  }
-  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], want_logc,
-                     want_threads));
+// Arguments of an elastic pass along axis slot k that do not depend on its launch shape.
+template <typename T>
+static ElArgs<T> el_args(const loss_ctx* h, Shot& s, int k, int pass_src, int do_B, int do_A, double acoef,
+                         double amp) {
   ElArgs<T> a{};
-  a.g = g;
   a.tb = Tables{s.W[k], h->t32, h->t64};
   int srcf[3];
-  switch (pass) {
-    case EL_BX:
-    case EL_BY: srcf[0] = LOSS_FIELD_V1, srcf[1] = LOSS_FIELD_V2, srcf[2] = LOSS_FIELD_V3; break;
-    case EL_BZ:
-      if (do_B) srcf[0] = LOSS_FIELD_V1, srcf[1] = LOSS_FIELD_V2, srcf[2] = LOSS_FIELD_V3;
-      else srcf[0] = LOSS_FIELD_S13, srcf[1] = LOSS_FIELD_S23, srcf[2] = LOSS_FIELD_S33;
-      break;
-    case EL_AX: srcf[0] = LOSS_FIELD_S11, srcf[1] = LOSS_FIELD_S12, srcf[2] = LOSS_FIELD_S13; break;
+  switch (pass_src) {
+    case 0: srcf[0] = LOSS_FIELD_V1, srcf[1] = LOSS_FIELD_V2, srcf[2] = LOSS_FIELD_V3; break;
+    case 1: srcf[0] = LOSS_FIELD_S13, srcf[1] = LOSS_FIELD_S23, srcf[2] = LOSS_FIELD_S33; break;
+    case 2: srcf[0] = LOSS_FIELD_S11, srcf[1] = LOSS_FIELD_S12, srcf[2] = LOSS_FIELD_S13; break;
     default: srcf[0] = LOSS_FIELD_S12, srcf[1] = LOSS_FIELD_S22, srcf[2] = LOSS_FIELD_S23; break;
   }
   for (int i = 0; i < 3; ++i) a.src[i] = (const T*)s.field[srcf[i]];
@@ -388,6 +371,72 @@ static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A,
   a.src_explosive = (s.src_kinds & LOSS_SRC_EXPLOSIVE) ? 1 : 0;
   a.src_shear = (s.src_kinds & LOSS_SRC_SHEAR_XZ) ? 1 : 0;
   a.force_mask = force_components(s.src_kinds);
+  return a;
+}
+
+// The FP32 y / z tile passes: the convolution family (loss_set_kernels), patches of at most 256 positions (at most
+// 16 warps: 8-position chunks up to M = 128, 16-position chunks above) and tiles within shared memory.
+static int elt_logc(const Shot& s, int k) { return (s.n[k] / s.p[k]) <= 128 ? 3 : 4; }
+static ElTile elt_geom(const Shot& s, int k) {
+  ElTile g{};
+  int threads;
+  g.t = tile_geom(s, k, &threads);
+  g.t.px = (k == 1) ? s.sy : s.sz;
+  g.t.Wd = s.Wd[k];
+  g.ostride = (k == 1) ? s.sz : s.sy;
+  g.nouter = (int)((k == 1) ? s.len[0] : s.len[1]);
+  g.nx = (int)s.len[2];
+  g.ncg = (g.nx + 31) / 32;
+  return g;
+}
+static bool elt_ok(const loss_ctx* h, const Shot& s) {
+  if (s.esize != 4 || !h->tiled || s.dim != 3) return false;
+  for (int k = 0; k < 2; ++k) {
+    const int M = (int)(s.n[k] / s.p[k]);
+    if (M > 256 || std::max(s.d.n_nb, FirLen<float>::K) > 64) return false;
+    if (elt_smem(elt_geom(s, k), elt_logc(s, k)) + 8192 > (size_t)h->smem_optin) return false;
+  }
+  return true;
+}
+
+template <bool K>
+static loss_status_t elt_pass(loss_ctx* h, Shot& s, int pass, double acoef, double amp) {
+  const int k = (pass == ET_BY || pass == ET_AY) ? 1 : 0;
+  LOSS_TRY(ensure_delta_weights(h, s, k));
+  const int src = (pass == ET_BY || pass == ET_BZ) ? 0 : (pass == ET_AZ ? 1 : 3);
+  const int do_B = (pass == ET_BY || pass == ET_BZ) ? 1 : 0;
+  const ElArgs<float> a = el_args<float>(h, s, k, src, do_B, 1 - do_B, acoef, amp);
+  const ElTile g = elt_geom(s, k);
+  LaunchScope ls(h, k == 1 ? LOSS_KERNEL_ELASTIC_Y : LOSS_KERNEL_ELASTIC_Z);
+  return cuda_check(h, launch_elt<K>(a, g, pass, elt_logc(s, k), h->stream), "elastic tile kernel");
+}
+
+template <typename T, bool K>
+static loss_status_t el_pass(loss_ctx* h, Shot& s, int pass, int do_B, int do_A, double acoef, double amp) {
+  // internal axis slot of the pass: x = 2, y = 1, z = 0
+  const int k = (pass == EL_BX || pass == EL_AX) ? 2 : ((pass == EL_BY || pass == EL_AY) ? 1 : 0);
+  LineGeom g;
+  int logc, threads;
+  const int kid = (k == 2) ? LOSS_KERNEL_ELASTIC_X : (k == 1 ? LOSS_KERNEL_ELASTIC_Y : LOSS_KERNEL_ELASTIC_Z);
+  // Built-in FP32 shapes of the elastic passes (what the autotuner picks on the 257^3 and 193^3 grids): chunks of
+  // 8 unknowns on every axis, 128 threads per x block and 256 per y / z block.
+  int want_threads = h->tile_threads[kid], want_logc = h->chunk_log2[kid];
+  if (sizeof(T) == 4 && h->lines_per_block[kid] <= 0) {
+    if (want_threads <= 0) want_threads = k == 2 ? 128 : 256;
+    if (want_logc <= 0) want_logc = 3;
+  }
+  LOSS_TRY(line_geom(h, s, k, s.sz, s.sy, &g, &logc, &threads, 6, 0, h->lines_per_block[kid], want_logc,
+                     want_threads));
+  int src;
+  switch (pass) {
+    case EL_BX:
+    case EL_BY: src = 0; break;
+    case EL_BZ: src = do_B ? 0 : 1; break;
+    case EL_AX: src = 2; break;
+    default: src = 3; break;
+  }
+  ElArgs<T> a = el_args<T>(h, s, k, src, do_B, do_A, acoef, amp);
+  a.g = g;
   LaunchScope ls(h, kid);
   return cuda_check(h, launch_el<T, K>(a, pass, logc, threads, h->stream), "elastic kernel");
 }
@@ -397,6 +446,11 @@ template <typename T, bool K>
 static loss_status_t elastic_A(loss_ctx* h, Shot& s, double tau, double force_t) {
   double famp = 0.0;
   if (s.src_on && (s.src_kinds & kForceMask)) famp = tau * s.src_norm * ricker(force_t, s.src_f0, s.src_t0);
+  if (sizeof(T) == 4 && elt_ok(h, s)) {
+    LOSS_TRY((elt_pass<K>(h, s, ET_AZ, tau, 0.0)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, tau, 0.0)));
+    return elt_pass<K>(h, s, ET_AY, tau, famp);
+  }
   LOSS_TRY((el_pass<T, K>(h, s, EL_BZ, 0, 1, tau, 0.0)));
   LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, tau, 0.0)));
   return el_pass<T, K>(h, s, EL_AY, 0, 1, tau, famp);
@@ -417,11 +471,20 @@ static loss_status_t elastic3d_step(loss_ctx* h, Shot& s) {
     amp = dt * s.src_norm * ricker(tn + 0.5 * dt, s.src_f0, s.src_t0);
   double famp = 0.0;
   if (s.src_on && (s.src_kinds & kForceMask)) famp = dt * s.src_norm * ricker(tn + dt, s.src_f0, s.src_t0);
-  LOSS_TRY((el_pass<T, K>(h, s, EL_BX, 1, 0, dt, 0.0)));
-  LOSS_TRY((el_pass<T, K>(h, s, EL_BY, 1, 0, dt, 0.0)));
-  LOSS_TRY((el_pass<T, K>(h, s, EL_BZ, 1, 1, dt, amp)));
-  LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, dt, 0.0)));
-  LOSS_TRY((el_pass<T, K>(h, s, EL_AY, 0, 1, dt, famp)));
+  if (sizeof(T) == 4 && elt_ok(h, s)) {
+    LOSS_TRY((el_pass<T, K>(h, s, EL_BX, 1, 0, dt, 0.0)));
+    LOSS_TRY((elt_pass<K>(h, s, ET_BY, dt, 0.0)));
+    LOSS_TRY((elt_pass<K>(h, s, ET_BZ, dt, amp)));
+    LOSS_TRY((elt_pass<K>(h, s, ET_AZ, dt, 0.0)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, dt, 0.0)));
+    LOSS_TRY((elt_pass<K>(h, s, ET_AY, dt, famp)));
+  } else {
+    LOSS_TRY((el_pass<T, K>(h, s, EL_BX, 1, 0, dt, 0.0)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_BY, 1, 0, dt, 0.0)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_BZ, 1, 1, dt, amp)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_AX, 0, 1, dt, 0.0)));
+    LOSS_TRY((el_pass<T, K>(h, s, EL_AY, 0, 1, dt, famp)));
+  }
   LOSS_TRY(gather_fields<T>(h, s, true, 1));
   LOSS_TRY(gather_fields<T>(h, s, false, 0));
   if (s.n_rcv) ++s.rcv_steps;

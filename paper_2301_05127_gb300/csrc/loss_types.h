@@ -266,6 +266,16 @@ struct TzShot {
 // Descriptor of one shot in a batched x launch: its rows come in units of R consecutive rows, the global units
 // unit0 .. unit0 + ceil(t.ncross / R) - 1.
 constexpr int kXpMaxGroups = 8;
+
+// Elastic y / z tile passes (FP32 truncated-convolution form).
+enum { ET_BY = 0, ET_BZ = 1, ET_AZ = 2, ET_AY = 3 };
+struct ElTile {
+  TileGeom t;       // the pass axis: n, p, M, H, Rd, Wd, s3h, r, a, rho, inv; t.px = stride along the axis
+  int64_t ostride;  // stride of the remaining axis (z for y tiles, y for z tiles)
+  int nouter;       // its extent
+  int ncg;          // groups of 32 x columns
+  int nx;           // x columns
+};
 struct XpShot {
   AcXArgs<float> a;
   TileGeom t;

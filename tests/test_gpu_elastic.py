@@ -25,8 +25,10 @@ def pkg():
     return p
 
 
-def _compare(pkg, w, prec, steps, every=20, fields=ELASTIC_FIELDS, traces=True):
+def _compare(pkg, w, prec, steps, every=20, fields=ELASTIC_FIELDS, traces=True, family=None):
     g = pkg.Grid.from_workloads([w], precision=prec)
+    if family:
+        g.set_kernels(family)
     sim = Simulation(w)
     peak = {f: 0.0 for f in fields}
     worst = {f: 0.0 for f in fields}
@@ -51,21 +53,23 @@ def _compare(pkg, w, prec, steps, every=20, fields=ELASTIC_FIELDS, traces=True):
     return errs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_kahan"])
-def test_homogeneous_small(pkg, prec):
-    """33^3 points in 2 x 2 x 2 patches, explosive + shear source, 6-point layer, 60 steps."""
+@pytest.mark.parametrize("prec,family", [("fp64", None), ("fp32", "convolution"), ("fp32", "line"),
+                                         ("fp32_kahan", "convolution"), ("fp32_kahan", "line")])
+def test_homogeneous_small(pkg, prec, family):
+    """33^3 points in 2 x 2 x 2 patches, explosive + shear source, 6-point layer, 60 steps; FP32 on both kernel
+    families (y / z passes on one-patch tiles in the truncated-convolution form, or on whole lines)."""
     w = elastic3d_homogeneous(n=32, p=2, n_nb=8, steps=60, pml_width=6, precision=prec)
     w = dataclasses.replace(w, f0=40.0, t0=1.2 / 40.0)
-    errs = _compare(pkg, w, prec, w.steps)
+    errs = _compare(pkg, w, prec, w.steps, family=family)
     assert max(errs.values()) < TOL[prec], errs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
-def test_heterogeneous_model(pkg, prec):
+@pytest.mark.parametrize("prec,family", [("fp64", None), ("fp32_kahan", "convolution"), ("fp32_kahan", "line")])
+def test_heterogeneous_model(pkg, prec, family):
     """Smooth random vp / vs / rho (arrays for lambda, mu and b), 4 x 4 x 4 patches of M = 12, 40 steps."""
     w = scaled(elastic3d_heterogeneous(), n=48, p=4, steps=40, n_nb=12, pml_width=8)
     w = dataclasses.replace(w, f0=40.0, t0=1.2 / 40.0)
-    errs = _compare(pkg, w, prec, w.steps)
+    errs = _compare(pkg, w, prec, w.steps, family=family)
     assert max(errs.values()) < TOL[prec], errs
 
 
@@ -82,6 +86,23 @@ def test_anisotropic_grid_force_source(pkg):
                             receivers={"v3": np.arange(33 * 41, dtype=np.int64)})
     errs = _compare(pkg, w, "fp64", w.steps)
     assert max(errs.values()) < TOL["fp64"], errs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_kahan"])
+def test_anisotropic_grid_three_forces_tiles(pkg, prec):
+    """Uneven n and p per axis (patches of 12, 16 and 10 points, shorter than the 20-point tile halo), the body
+    force along x, y and z plus the explosive source, 30 steps, on the FP32 tile passes."""
+    w = elastic3d_homogeneous(n=32, p=2, n_nb=8, steps=30, pml_width=4, precision=prec)
+    shape = (25, 33, 41)
+
+    def model():
+        return np.full(shape, 3000.0), np.full(shape, 1730.0), np.full(shape, 2000.0)
+
+    w = dataclasses.replace(w, n=(24, 32, 40), p=(2, 2, 4), model_fn=model, src_index=(12, 16, 20),
+                            src_kinds=("force_x", "force_y", "force_z", "explosive"), f0=40.0, t0=1.2 / 40.0,
+                            receivers={"v1": np.arange(33 * 41, dtype=np.int64)})
+    errs = _compare(pkg, w, prec, w.steps, family="convolution")
+    assert max(errs.values()) < TOL[prec], errs
 
 
 def test_full_size_homogeneous_one_step(pkg):
