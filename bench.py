@@ -18,6 +18,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -119,7 +120,7 @@ class Clocks:
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -129,7 +130,9 @@ class Clocks:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and the throttle reasons seen; window = (t0, t1) in time.time() seconds keeps only the
+        samples taken inside it (all samples when none falls inside)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -137,18 +140,28 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+        if window is not None:
+            inside = [r for r in rows if r[0] is not None and window[0] - 0.25 <= r[0] <= window[1] + 0.25]
+            rows = inside or rows
+        sm = [r[1] for r in rows]
+        smax = [r[2] for r in rows]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[3]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
@@ -379,17 +392,20 @@ def run_ours(args):
 
     # --- headline: FP32 + Kahan -------------------------------------------------------------------------
     g = pkg.Grid.from_workloads([w])
+    # the clock sampler starts before the warm-up steps: starting a process inside the timed region would delay
+    # the first timed step's launches
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.5)
     g.step(args.warmup)
     g.sync()
     g.profile(False)  # counts launches, records no per-launch events
-    clk = Clocks(local)
     barrier()
-    clk.start()
-    t_wall = time.perf_counter()
+    t_wall, t_start = time.perf_counter(), time.time()
     step_ms = _timed_steps(torch, g, args.steps, flush)
     barrier()
     t_wall = time.perf_counter() - t_wall
-    clocks = clk.stop()
+    clocks = clk.stop(window=(t_start, time.time()))
     launches = g.profile_read(-1)[1]
     # kernel durations: K more steps, flushed the same way, with a CUDA event pair around every launch on the
     # library's stream (the events cost ~2 us per launch, so they are kept out of the headline steps)

@@ -257,13 +257,54 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
 //   ET_AY (y):  v_i += b (U_i + Y[s_i2, y]) (as EL_AY), + body force
 // Tiles are independent: no block holds a whole line.  The z part of the velocity sub-step is a pass of its own
 // (the line kernel computes it on the stresses BZ leaves on chip; a tile has no neighbour's new stresses).
+// Junction corrections of the three staged fields of a tile: D[s][J] = sum_m Wd[J][m] f_s[jM + m] for the tile's two
+// junctions J, accumulated in FP64 with the 32 columns on the lanes.  Items (field, junction, tap subset) go round
+// the warps (ns = min(8, max(1, warps / 6)) subsets per field and junction); partial sums meet in partf.  Contains
+// no barrier: partf is complete after the caller's next barrier, and elt_junction_reduce then forms dl.
+__device__ __forceinline__ void elt_junction_parts(const float* __restrict__ F, int fstride, const ZBun& bun,
+                                                   int nvalid, int l, const TileGeom& t, int ns,
+                                                   const double* __restrict__ wsm, double* __restrict__ partf) {
+  const int col = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int wl = 2 * t.Rd + 1;
+  for (int it = w; it < 6 * ns; it += nw) {  // item = ((field, junction), subset)
+    const int fj = it % 6, sub = it / 6;
+    const int s = fj >> 1, J = fj & 1;
+    const int c = (l + J) * t.M;
+    const int mlo = max(-t.Rd, -c);
+    const int mhi = min(t.Rd, t.n - c);
+    const double* wj = wsm + J * wl + t.Rd;
+    const float* Fs = F + s * fstride;
+    double a = 0.0, b = 0.0;  // two independent accumulators halve the FP64 dependency chain
+    if (col < nvalid) {
+      int m = mlo + sub;
+      for (; m + ns <= mhi; m += 2 * ns) {
+        a = fma(wj[m], widen(Fs[bun.at(col, c + m)]), a);
+        b = fma(wj[m + ns], widen(Fs[bun.at(col, c + m + ns)]), b);
+      }
+      if (m <= mhi) a = fma(wj[m], widen(Fs[bun.at(col, c + m)]), a);
+    }
+    partf[(fj * ns + sub) * 32 + col] = a + b;
+  }
+}
+__device__ __forceinline__ void elt_junction_reduce(const double* __restrict__ partf, int ns, float* __restrict__ dl) {
+  for (int i = threadIdx.x; i < 6 * 32; i += blockDim.x) {  // (field, junction) x column
+    const int fj = i >> 5, cl = i & 31;
+    double acc = 0.0;
+    for (int q = 0; q < ns; ++q) acc += partf[(fj * ns + q) * 32 + cl];
+    dl[(fj >> 1) * 64 + 2 * cl + (fj & 1)] = (float)acc;
+  }
+}
+
+// 8-position chunks up to M = 64 (at most 8 warps, 3 blocks per SM), 16-position chunks up to M = 256.
 template <int PASS, bool KAHAN, int LOGC>
-__global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
+__global__ void __launch_bounds__(LOGC == 3 ? 256 : 512, LOGC == 3 ? 3 : 1) k_elt(ElArgs<float> a, ElTile g) {
   constexpr int C = 1 << LOGC;
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float rpow[kFirPow];
-  __shared__ float dl[3][64];
-  __shared__ double jpart[16 * 32];
+  __shared__ float dl[3 * 64];
+  __shared__ double partf[6 * 8 * 32];
   __shared__ double wsm[2 * 129];
   const TileGeom& t = g.t;
   const int l = blockIdx.x % t.p;
@@ -277,9 +318,10 @@ __global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
   const int nch = (t.M + C - 1) / C;
   const bool last = l == t.p - 1;
   const int64_t obase = (int64_t)outer * g.ostride + x0;
+  const int fstride = rows * 32;
   float* F = reinterpret_cast<float*>(sm);  // three fields, [rows][32] each
-  float* PA = F + 3 * rows * 32;            // [chunk][32] warm-up partial sums
-  float* PB = PA + nch * 32;
+  float* PA = F + 3 * fstride;              // [field][chunk][32] warm-up partial sums
+  float* PB = PA + 3 * nch * 32;
   fill_rpow(rpow, t.r);
   {
     const int wl = 2 * t.Rd + 1;
@@ -287,7 +329,7 @@ __global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
   }
   for (int s = 0; s < 3; ++s) {
     const float* f = a.src[s] + obase;
-    float* Fs = F + s * rows * 32;
+    float* Fs = F + s * fstride;
     for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
       const int q = i >> 3, seg = i & 7;
       const int pos = zb + q;
@@ -299,53 +341,54 @@ __global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
   __syncthreads();
   const ZBun bun{zb};
   const int nvalid = min(32, g.nx - x0);
-  const int nwj = blockDim.x >> 5;
-  for (int s = 0; s < 3; ++s) {
-    tile_junctions_z(F + s * rows * 32, bun, nvalid, l, t, nwj, wsm, jpart, dl[s]);
-    __syncthreads();
-  }
+  const int ns = min(8, max(1, (int)(blockDim.x >> 5) / 6));
   const int col = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;
   const int p0 = z0 + c * C;
   const int len = min(C, z0 + t.M - p0);
   const int lenx = len + ((len > 0 && last && p0 + len == t.n) ? 1 : 0);  // with the line's last point
   const bool mine = len > 0 && col < nvalid;
+  // one phase for the FP64 junction sums and the warm-up partial sums of all three fields
+  elt_junction_parts(F, fstride, bun, nvalid, l, t, ns, wsm, partf);
+  if (mine && len == C) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      float fv[C + 1];
+#pragma unroll
+      for (int j = 0; j < C; ++j) fv[j] = F[s * fstride + bun.at(col, p0 + j)];
+      chunk_partials<C>(fv, t.r, PA[(s * nch + c) * 32 + col], PB[(s * nch + c) * 32 + col]);
+    }
+  }
+  __syncthreads();
+  elt_junction_reduce(partf, ns, dl);
+  __syncthreads();
   constexpr int W = FirLen<float>::K / C;
   const float rC = rpow[C];
-  // each field's derivative of the chunk replaces the field's own rows in the tile once every warm-up read of
-  // them is done; a thread reads back only what it wrote
+  float e[3][C + 1];
+  if (mine) {
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    float* Fs = F + s * rows * 32;
-    float fv[C + 1], e[C + 1];
-    if (mine) {
+    for (int s = 0; s < 3; ++s) {
+      const float* Fs = F + s * fstride;
+      const float* PAs = PA + s * nch * 32;
+      const float* PBs = PB + s * nch * 32;
+      float fv[C + 1];
 #pragma unroll
       for (int j = 0; j <= C; ++j)
         if (j < lenx) fv[j] = Fs[bun.at(col, p0 + j)];
-      if (len == C) chunk_partials<C>(fv, t.r, PA[c * 32 + col], PB[c * 32 + col]);
-    }
-    __syncthreads();
-    if (mine) {
       float sL, qR;
       if (c >= W) {
-        sL = PA[(c - 1) * 32 + col];
-        if (W == 2) sL += rC * PA[(c - 2) * 32 + col];
+        sL = PAs[(c - 1) * 32 + col];
+        if (W == 2) sL += rC * PAs[(c - 2) * 32 + col];
       } else {
         sL = fir_left<float, FirLen<float>::K>(Fs, bun, col, p0, t.n, t.r);
       }
       if (lenx == C && (c + W + 1) * C <= t.M) {
-        qR = PB[(c + 1) * 32 + col];
-        if (W == 2) qR += rC * PB[(c + 2) * 32 + col];
+        qR = PBs[(c + 1) * 32 + col];
+        if (W == 2) qR += rC * PBs[(c + 2) * 32 + col];
       } else {
         qR = fir_right<float, FirLen<float>::K>(Fs, bun, col, p0 + lenx - 1, t.n, t.r);
       }
-      tile_chunk_e<C>(fv, p0, lenx, z0, t, dl[s] + 2 * col, rpow, sL, qR, e);
-    }
-    __syncthreads();
-    if (mine) {
-#pragma unroll
-      for (int j = 0; j <= C; ++j)
-        if (j < lenx) Fs[bun.at(col, p0 + j)] = e[j];
+      tile_chunk_e<C>(fv, p0, lenx, z0, t, dl + s * 64 + 2 * col, rpow, sL, qR, e[s]);
     }
   }
   if (!mine) return;
@@ -356,8 +399,7 @@ __global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
     if (j >= lenx) break;
     const int pos = p0 + j;
     const int64_t gi = obase + (int64_t)pos * t.px + col;
-    const int k = bun.at(col, pos);
-    const float g0 = s3h * F[k], g1 = s3h * F[rows * 32 + k], g2 = s3h * F[2 * rows * 32 + k];
+    const float g0 = s3h * e[0][j], g1 = s3h * e[1][j], g2 = s3h * e[2][j];
     if (PASS == ET_BY) {
       const float t1 = tt[1][gi];
       const float y0 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt);
@@ -440,7 +482,7 @@ __global__ void __launch_bounds__(512, 1) k_elt(ElArgs<float> a, ElTile g) {
 size_t elt_smem(const ElTile& g, int logc) {
   const int rows = g.t.M + 2 * g.t.H + 1;
   const int nch = (g.t.M + (1 << logc) - 1) >> logc;
-  return (size_t)3 * rows * 32 * 4 + (size_t)2 * nch * 32 * 4;
+  return (size_t)3 * rows * 32 * 4 + (size_t)6 * nch * 32 * 4;
 }
 
 template <int PASS, bool KAHAN>

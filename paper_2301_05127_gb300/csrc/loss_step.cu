@@ -374,9 +374,9 @@ static ElArgs<T> el_args(const loss_ctx* h, Shot& s, int k, int pass_src, int do
   return a;
 }
 
-// The FP32 y / z tile passes: the convolution family (loss_set_kernels), patches of at most 256 positions (at most
-// 16 warps: 8-position chunks up to M = 128, 16-position chunks above) and tiles within shared memory.
-static int elt_logc(const Shot& s, int k) { return (s.n[k] / s.p[k]) <= 128 ? 3 : 4; }
+// The FP32 y / z tile passes: the convolution family (loss_set_kernels), patches of at most 256 positions (8-position
+// chunks up to M = 64, at most 8 warps; 16-position chunks above, at most 16 warps) and tiles within shared memory.
+static int elt_logc(const Shot& s, int k) { return (s.n[k] / s.p[k]) <= 64 ? 3 : 4; }
 static ElTile elt_geom(const Shot& s, int k) {
   ElTile g{};
   int threads;

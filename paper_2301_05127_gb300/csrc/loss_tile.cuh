@@ -33,9 +33,9 @@ __device__ __forceinline__ void fill_rpow(float* rpow, float r) {
 // ready after the caller's next barrier.
 // nwj: the warp count that fixes the tap subsets (the single-shot launch's), so that every launch shape sums in the
 // same order.
-__device__ inline void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, int nvalid, int jg, const TileGeom& t,
-                                 int nwj, const double* __restrict__ wsm, double* __restrict__ partf,
-                                 float* __restrict__ dl) {
+__device__ inline void tile_junctions_z(const float* __restrict__ F, const ZBun& bun, int nvalid, int jg,
+                                        const TileGeom& t, int nwj, const double* __restrict__ wsm,
+                                        double* __restrict__ partf, float* __restrict__ dl) {
   const int col = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
