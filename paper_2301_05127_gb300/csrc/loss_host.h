@@ -12,6 +12,11 @@
 namespace lossk {
 
 constexpr int kTableLen = 64;
+// Rounding error of v rounded to T, rounded to T (0 for double): the low part of a coefficient for mulc.
+template <typename T>
+inline T lo_part(double v) {
+  return (T)(v - (double)(T)v);
+}
 // Body-force source kinds (f_1, f_2, f_3) and the component of each.
 constexpr uint32_t kForceMask = LOSS_SRC_FORCE_X | LOSS_SRC_FORCE_Y | LOSS_SRC_FORCE_Z;
 inline int force_components(uint32_t kinds) {

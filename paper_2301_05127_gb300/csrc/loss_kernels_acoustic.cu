@@ -156,10 +156,10 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
       // scalar update of one point (PML layers, source block, line tail)
       auto one = [&](int pos) {
         const int64_t gi = rb + pos;
-        const T gx = a.s3h * O[bun.at(l, pos)];  // d_x v1
+        const T gx = mulc(O[bun.at(l, pos)], a.s3h, a.s3h_lo);  // d_x v1
         const T gz = stl[pos];                   // d_z v3
-        T inc = (a.pml && a.xB.in(pos)) ? a.xB.step(a.phix, gi, pos, gx) : -a.dt * gx;
-        inc += zlay ? a.zB.step(a.phiz, gi, z, gz) : -a.dt * gz;
+        T inc = (a.pml && a.xB.in(pos)) ? a.xB.step(a.phix, gi, pos, gx) : -mulc(gx, a.dt, a.dt_lo);
+        inc += zlay ? a.zB.step(a.phiz, gi, z, gz) : -mulc(gz, a.dt, a.dt_lo);
         T delta = skl[pos] * inc;
         if (srow) {
           const int dx = pos - a.src.xs + 12;
@@ -202,7 +202,7 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
             if (pos < np) one(pos);
             continue;
           }
-          const T delta = kp[t] * (-a.dt * (a.s3h * ox[t] + gz[t]));
+          const T delta = kp[t] * -mulc(mulc(ox[t], a.s3h, a.s3h_lo) + gz[t], a.dt, a.dt_lo);
           if constexpr (KAHAN) {
             kahan_add(sg[t], cc[t], delta);
             a.csig[rb + pos] = cc[t];
@@ -230,7 +230,7 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
       const T* svl = SV + l * sp;
       auto one = [&](int pos) {
         const int64_t gi = rb + pos;
-        const T gx = a.s3h * O[bun.at(l, pos)];  // d_x sigma
+        const T gx = mulc(O[bun.at(l, pos)], a.s3h, a.s3h_lo);  // d_x sigma
         const T bb = a.b ? a.b[gi] : a.b0;
         T inc;
         if (a.pml && a.xA.in(pos)) {
@@ -238,9 +238,9 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
           inc = a.xA.step(a.psix, gi, pos, gx);
           if (a.dlt) a.dlt[gi] = bb * (ih - T(0.5) * inc);
         } else {
-          inc = -a.acoef * gx;
+          inc = -mulc(gx, a.acoef, a.acoef_lo);
         }
-        const T delta = bb * inc;
+        const T delta = a.b ? bb * inc : mulc(inc, a.b0, a.b0_lo);
         T v = V[bun.at(l, pos)];
         if constexpr (KAHAN) {
           float c = svl[pos];
@@ -252,8 +252,7 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
         a.v1[gi] = v;
       };
       const int T4 = 4 * blockDim.x;
-      const T sc = -a.acoef * a.b0 * a.s3h;
-      for (int q0 = threadIdx.x; q0 < np; q0 += T4) {
+            for (int q0 = threadIdx.x; q0 < np; q0 += T4) {
         T ox[4], vv[4], cc[4];
         bool fastp[4];
 #pragma unroll
@@ -274,7 +273,7 @@ __device__ __forceinline__ void ac_x_tile(const AcXArgs<T>& a, int bid, unsigned
             if (pos < np) one(pos);
             continue;
           }
-          const T delta = sc * ox[t];
+          const T delta = mulc(ox[t], a.sc, a.sc_lo);
           if constexpr (KAHAN) {
             kahan_add(vv[t], cc[t], delta);
             a.cv1[rb + pos] = cc[t];
@@ -330,7 +329,7 @@ __device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned
   const int wl = g.L >= 4 ? 4 : g.L;        // lines per item
   auto one = [&](int l, int pos) {
     const int64_t gi = cv.lb[l] + (int64_t)pos * g.pstride;
-    const T gz = a.s3h * O[bun.at(l, pos)];  // d_z sigma
+    const T gz = mulc(O[bun.at(l, pos)], a.s3h, a.s3h_lo);  // d_z sigma
     const T bb = a.b ? a.b[gi] : a.b0;
     T inc;
     if (a.pml && a.zA.in(pos)) {
@@ -338,9 +337,9 @@ __device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned
       inc = a.zA.step(a.psiz, gi, pos, gz);
       if (a.dlt) a.dlt[gi] = bb * (ih - T(0.5) * inc);
     } else {
-      inc = -a.acoef * gz;
+      inc = -mulc(gz, a.acoef, a.acoef_lo);
     }
-    const T delta = bb * inc;
+    const T delta = a.b ? bb * inc : mulc(inc, a.b0, a.b0_lo);
     T vv = a.v3[gi];
     if constexpr (KAHAN) {
       float cc = a.cv3[gi];
@@ -353,8 +352,7 @@ __device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned
     S[bun.at(l, pos)] = vv;
   };
   const int items = np << lg;
-  const T sc = -a.acoef * a.b0 * a.s3h;
-  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    for (int i = threadIdx.x; i < items; i += blockDim.x) {
     const int pos = i >> lg;
     const int l0 = (i & ((1 << lg) - 1)) * wl;
     if (g.L < 4 || l0 + 3 >= nvalid || a.b || (a.pml && a.zA.in(pos))) {
@@ -370,7 +368,7 @@ __device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned
     ld4(O + k, o);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const T delta = sc * o[t];
+      const T delta = mulc(o[t], a.sc, a.sc_lo);
       if constexpr (KAHAN) {
         kahan_add(v[t], c[t], delta);
       } else {
@@ -392,13 +390,13 @@ __device__ __forceinline__ void ac_z_tile(const AcZArgs<T>& a, int bid, unsigned
     const int l0 = (i & ((1 << lg) - 1)) * wl;
     if (g.L < 4 || l0 + 3 >= nvalid) {
       for (int t = 0; t < wl; ++t)
-        if (l0 + t < nvalid) a.tmp[cv.lb[l0 + t] + (int64_t)pos * g.pstride] = a.s3h * O[bun.at(l0 + t, pos)];
+        if (l0 + t < nvalid) a.tmp[cv.lb[l0 + t] + (int64_t)pos * g.pstride] = mulc(O[bun.at(l0 + t, pos)], a.s3h, a.s3h_lo);
       continue;
     }
     T o[4];
     ld4(O + bun.at(l0, pos), o);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) o[t] *= a.s3h;
+    for (int t = 0; t < 4; ++t) o[t] = mulc(o[t], a.s3h, a.s3h_lo);
     st4(a.tmp + cv.lb[l0] + (int64_t)pos * g.pstride, o);
   }
 }

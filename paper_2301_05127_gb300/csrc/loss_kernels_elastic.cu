@@ -29,15 +29,15 @@ size_t smem_bytes(const LineGeom& g, int nbuf, int nstage, size_t esize);  // lo
 
 // tau times the (stretched) derivative g along this pass's axis at line position pos.
 template <typename T>
-__device__ __forceinline__ T eff(int pml, const PmlAxis<T>& pa, T* mem, int64_t gi, int pos, T g, T tau) {
-  return (pml && pa.in(pos)) ? -pa.step(mem, gi, pos, g) : tau * g;
+__device__ __forceinline__ T eff(int pml, const PmlAxis<T>& pa, T* mem, int64_t gi, int pos, T g, T tau, T tau_lo) {
+  return (pml && pa.in(pos)) ? -pa.step(mem, gi, pos, g) : mulc(g, tau, tau_lo);
 }
 
 // Velocity-sub-step term: returns tau * (stretched derivative); in a layer with receiver corrections on, also
 // stores b (X(tau/2) - X(tau)/2), the amount by which the first half of the step differs from half of it.
 template <typename T>
 __device__ __forceinline__ T effA(const ElArgs<T>& a, int term, int64_t gi, int pos, T g, T tau) {
-  if (!(a.pml && a.pA.in(pos))) return tau * g;
+  if (!(a.pml && a.pA.in(pos))) return mulc(g, tau, a.acoef_lo);
   T xh = T(0);
   const bool rec = a.dlt[term] != nullptr;
   if (rec) xh = -a.pA.half(a.memA[term], gi, pos, g);
@@ -125,17 +125,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
   if (PASS == EL_BX) {
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
-      t[0][gi] = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
-      t[1][gi] = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
-      t[2][gi] = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+      t[0][gi] = eff(a.pml, a.pB, a.memB[0], gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
+      t[1][gi] = eff(a.pml, a.pB, a.memB[1], gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
+      t[2][gi] = eff(a.pml, a.pB, a.memB[2], gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
     });
   } else if (PASS == EL_BY) {
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
       const T t1 = t[1][gi];  // loaded before any store (see EL_BZ)
-      const T x0 = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);
-      const T x1 = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);
-      const T x2 = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);
+      const T x0 = eff(a.pml, a.pB, a.memB[0], gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
+      const T x1 = eff(a.pml, a.pB, a.memB[1], gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
+      const T x2 = eff(a.pml, a.pB, a.memB[2], gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), dt, a.dt_lo);
       t[1][gi] = t1 + x0;
       t[3][gi] = x1;
       t[4][gi] = x2;
@@ -159,12 +159,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
         const T xa = t[0][gi], xd = t[3][gi], tc = t[2][gi], tb = t[1][gi], te = t[4][gi];
         const T lam = a.lam ? a.lam[gi] : a.lam0;
         const T mu = a.mu ? a.mu[gi] : a.mu0;
-        const T x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, a.s3h * O[0][k], dt);  // v1 along z
-        const T x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, a.s3h * O[1][k], dt);  // v2 along z
-        const T x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, a.s3h * O[2][k], dt);  // v3 along z
-        const T ltr = lam * (xa + xd + x33);
-        T s11 = ltr + T(2) * mu * xa, s22 = ltr + T(2) * mu * xd, s33 = ltr + T(2) * mu * x33;
-        T s13 = mu * (tc + x13);
+        const T x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), dt, a.dt_lo);  // v1 along z
+        const T x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), dt, a.dt_lo);  // v2 along z
+        const T x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), dt, a.dt_lo);  // v3 along z
+        // constant moduli enter through mulc (their rounding errors would bias every update the same way)
+        auto mlam = [&](T x) { return a.lam ? lam * x : mulc(x, a.lam0, a.lam0_lo); };
+        auto mmu = [&](T x) { return a.mu ? mu * x : mulc(x, a.mu0, a.mu0_lo); };
+        const T ltr = mlam(xa + xd + x33);
+        T s11 = ltr + T(2) * mmu(xa), s22 = ltr + T(2) * mmu(xd), s33 = ltr + T(2) * mmu(x33);
+        T s13 = mmu(tc + x13);
         if (a.srcp.on) {
           const int dz = pos - a.srcp.zs + 12, dy = outer - a.srcp.ys + 12, dx = x0 + l - a.srcp.xs + 12;
           if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u) {
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
             if (a.src_shear) s13 += sv;
           }
         }
-        const T d[6] = {s11, s22, mu * tb, s13, mu * (te + x23), s33};
+        const T d[6] = {s11, s22, mmu(tb), s13, mmu(te + x23), s33};
 #pragma unroll
         for (int f = 0; f < 6; ++f) upd_r<T, KAHAN>(u[f], cu[f], d[f]);
 #pragma unroll
@@ -193,18 +196,18 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
     if (a.do_A) {
       for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
         const int k = bun.at(l, pos);
-        t[5][gi] = effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
-        t[6][gi] = effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
-        t[7][gi] = effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+        t[5][gi] = effA(a, 0, gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), ta);
+        t[6][gi] = effA(a, 1, gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), ta);
+        t[7][gi] = effA(a, 2, gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), ta);
       });
     }
   } else if (PASS == EL_AX) {
     for_points<SFLAV>(g, cv.lb, nvalid, logL, [&](int l, int pos, int64_t gi) {
       const int k = bun.at(l, pos);
       const T t5 = t[5][gi], t6 = t[6][gi], t7 = t[7][gi];  // loaded before any store (see EL_BZ)
-      const T y0 = effA(a, 0, gi, pos, a.s3h * O[0][k], ta);
-      const T y1 = effA(a, 1, gi, pos, a.s3h * O[1][k], ta);
-      const T y2 = effA(a, 2, gi, pos, a.s3h * O[2][k], ta);
+      const T y0 = effA(a, 0, gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), ta);
+      const T y1 = effA(a, 1, gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), ta);
+      const T y2 = effA(a, 2, gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), ta);
       t[5][gi] = t5 + y0;
       t[6][gi] = t6 + y1;
       t[7][gi] = t7 + y2;
@@ -230,9 +233,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024) k_el(ElArgs<T> a)
         cu[f] = KAHAN ? a.cmp[LOSS_FIELD_V1 + f][gi] : T(0);
       }
       const T t5 = t[5][gi], t6 = t[6][gi], t7 = t[7][gi];
-      const T d0 = b * (t5 + effA(a, 0, gi, pos, a.s3h * O[0][k], ta) + f0);
-      const T d1 = b * (t6 + effA(a, 1, gi, pos, a.s3h * O[1][k], ta) + f1);
-      const T d2 = b * (t7 + effA(a, 2, gi, pos, a.s3h * O[2][k], ta) + f2);
+      auto mb = [&](T x) { return a.b ? b * x : mulc(x, a.b0, a.b0_lo); };
+      const T d0 = mb(t5 + effA(a, 0, gi, pos, mulc(O[0][k], a.s3h, a.s3h_lo), ta) + f0);
+      const T d1 = mb(t6 + effA(a, 1, gi, pos, mulc(O[1][k], a.s3h, a.s3h_lo), ta) + f1);
+      const T d2 = mb(t7 + effA(a, 2, gi, pos, mulc(O[2][k], a.s3h, a.s3h_lo), ta) + f2);
       upd_r<T, KAHAN>(u[0], cu[0], d0);
       upd_r<T, KAHAN>(u[1], cu[1], d1);
       upd_r<T, KAHAN>(u[2], cu[2], d2);
@@ -399,12 +403,13 @@ __global__ void __launch_bounds__(LOGC == 3 ? 256 : 512, LOGC == 3 ? 3 : 1) k_el
     if (j >= lenx) break;
     const int pos = p0 + j;
     const int64_t gi = obase + (int64_t)pos * t.px + col;
-    const float g0 = s3h * e[0][j], g1 = s3h * e[1][j], g2 = s3h * e[2][j];
+    const float g0 = mulc(e[0][j], s3h, t.s3h_lo), g1 = mulc(e[1][j], s3h, t.s3h_lo),
+                g2 = mulc(e[2][j], s3h, t.s3h_lo);
     if (PASS == ET_BY) {
       const float t1 = tt[1][gi];
-      const float y0 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt);
-      const float y1 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt);
-      const float y2 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt);
+      const float y0 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt, a.dt_lo);
+      const float y1 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt, a.dt_lo);
+      const float y2 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt, a.dt_lo);
       tt[1][gi] = t1 + y0;
       tt[3][gi] = y1;
       tt[4][gi] = y2;
@@ -421,12 +426,14 @@ __global__ void __launch_bounds__(LOGC == 3 ? 256 : 512, LOGC == 3 ? 3 : 1) k_el
       const float xa = tt[0][gi], xd = tt[3][gi], tc = tt[2][gi], tb = tt[1][gi], te = tt[4][gi];
       const float lam = a.lam ? a.lam[gi] : a.lam0;
       const float mu = a.mu ? a.mu[gi] : a.mu0;
-      const float x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt);  // v1 along z
-      const float x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt);  // v2 along z
-      const float x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt);  // v3 along z
-      const float ltr = lam * (xa + xd + x33);
-      float s11 = ltr + 2.0f * mu * xa, s22 = ltr + 2.0f * mu * xd, s33 = ltr + 2.0f * mu * x33;
-      float s13 = mu * (tc + x13);
+      const float x13 = eff(a.pml, a.pB, a.memB[0], gi, pos, g0, dt, a.dt_lo);  // v1 along z
+      const float x23 = eff(a.pml, a.pB, a.memB[1], gi, pos, g1, dt, a.dt_lo);  // v2 along z
+      const float x33 = eff(a.pml, a.pB, a.memB[2], gi, pos, g2, dt, a.dt_lo);  // v3 along z
+      auto mlam = [&](float x) { return a.lam ? lam * x : mulc(x, a.lam0, a.lam0_lo); };
+      auto mmu = [&](float x) { return a.mu ? mu * x : mulc(x, a.mu0, a.mu0_lo); };
+      const float ltr = mlam(xa + xd + x33);
+      float s11 = ltr + 2.0f * mmu(xa), s22 = ltr + 2.0f * mmu(xd), s33 = ltr + 2.0f * mmu(x33);
+      float s13 = mmu(tc + x13);
       if (a.srcp.on) {
         const int dz = pos - a.srcp.zs + 12, dy = outer - a.srcp.ys + 12, dx = x0 + col - a.srcp.xs + 12;
         if ((unsigned)dz < 25u && (unsigned)dy < 25u && (unsigned)dx < 25u) {
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(LOGC == 3 ? 256 : 512, LOGC == 3 ? 3 : 1) k_el
           if (a.src_shear) s13 += sv;
         }
       }
-      const float d[6] = {s11, s22, mu * tb, s13, mu * (te + x23), s33};
+      const float d[6] = {s11, s22, mmu(tb), s13, mmu(te + x23), s33};
 #pragma unroll
       for (int f = 0; f < 6; ++f) upd_r<float, KAHAN>(u[f], cu[f], d[f]);
 #pragma unroll
@@ -464,9 +471,10 @@ __global__ void __launch_bounds__(LOGC == 3 ? 256 : 512, LOGC == 3 ? 3 : 1) k_el
         cu[f] = KAHAN ? a.cmp[LOSS_FIELD_V1 + f][gi] : 0.0f;
       }
       const float t5 = tt[5][gi], t6 = tt[6][gi], t7 = tt[7][gi];
-      const float d0 = b * (t5 + effA(a, 0, gi, pos, g0, ta) + f0);
-      const float d1 = b * (t6 + effA(a, 1, gi, pos, g1, ta) + f1);
-      const float d2 = b * (t7 + effA(a, 2, gi, pos, g2, ta) + f2);
+      auto mb = [&](float x) { return a.b ? b * x : mulc(x, a.b0, a.b0_lo); };
+      const float d0 = mb(t5 + effA(a, 0, gi, pos, g0, ta) + f0);
+      const float d1 = mb(t6 + effA(a, 1, gi, pos, g1, ta) + f1);
+      const float d2 = mb(t7 + effA(a, 2, gi, pos, g2, ta) + f2);
       upd_r<float, KAHAN>(u[0], cu[0], d0);
       upd_r<float, KAHAN>(u[1], cu[1], d1);
       upd_r<float, KAHAN>(u[2], cu[2], d2);

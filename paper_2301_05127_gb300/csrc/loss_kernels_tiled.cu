@@ -144,7 +144,7 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
       if (j >= len) break;
       const int pos = p0 + j;
       const int64_t gi = (int64_t)pos * t.px + base;
-      const float gz = t.s3h * e[j];
+      const float gz = mulc(e[j], t.s3h, t.s3h_lo);
       if (MODE == 2) {
         a.tmp[gi] = gz;
         continue;
@@ -156,9 +156,9 @@ __device__ __forceinline__ void tz_tile(const AcZArgs<float>& a, const TileGeom&
         inc = a.zA.step(a.psiz, gi, pos, gz);
         if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
       } else {
-        inc = -a.acoef * gz;
+        inc = -mulc(gz, a.acoef, a.acoef_lo);
       }
-      const float delta = bb * inc;
+      const float delta = a.b ? bb * inc : mulc(inc, a.b0, a.b0_lo);
       const int k = (pos - z0) * 32 + col;
       float v = SV[k];
       if (KAHAN) {
@@ -462,7 +462,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
         if (ob >= 0) {
 #pragma unroll
           for (int j = 0; j < 9; ++j)
-            if (j < len) O[9 * ob + j] = t.s3h * e[j];
+            if (j < len) O[9 * ob + j] = mulc(e[j], t.s3h, t.s3h_lo);
         } else {
           float sg[9], cs[9], kp[9], gz[9], iz[9];
           {
@@ -502,12 +502,12 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
             store_run<8>(a.phiz + rb + p0, len, pz);
           } else {
 #pragma unroll
-            for (int j = 0; j < 9; ++j) iz[j] = -a.dt * gz[j];
+            for (int j = 0; j < 9; ++j) iz[j] = -mulc(gz[j], a.dt, a.dt_lo);
           }
 #pragma unroll
           for (int j = 0; j < 9; ++j) {
             if (j >= len) break;
-            const float delta = kp[j] * (-a.dt * (t.s3h * e[j]) + iz[j]);
+            const float delta = kp[j] * (-mulc(mulc(e[j], t.s3h, t.s3h_lo), a.dt, a.dt_lo) + iz[j]);
             float v = sg[j];
             if (KAHAN) {
               float cc = cs[j];
@@ -539,12 +539,12 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       const int k = lay.bun.at(0, pos);
       const float gx = O[q];
       const float gzv = ST[k];
-      float inc = -a.dt * gx;
+      float inc = -mulc(gx, a.dt, a.dt_lo);
       if (a.pml && a.xB.in(pos)) {
         const int sl = ms.at(pos);
         inc = pml_step_s(tabs, F, sl, segB[sl], gx, a.phix, gi);
       }
-      const float incz = zlay ? a.zB.step(a.phiz, gi, row, gzv) : -a.dt * gzv;
+      const float incz = zlay ? a.zB.step(a.phiz, gi, row, gzv) : -mulc(gzv, a.dt, a.dt_lo);
       float delta = SK[k] * (inc + incz);
       if (srow) {
         const int dx = pos - a.src.xs + 12;
@@ -582,7 +582,7 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       if (oa >= 0) {
 #pragma unroll
         for (int j = 0; j < 9; ++j)
-          if (j < len) O[9 * oa + j] = t.s3h * e[j];
+          if (j < len) O[9 * oa + j] = mulc(e[j], t.s3h, t.s3h_lo);
       } else {
         float vv[9], cs[9], bb[9];
         {
@@ -605,7 +605,8 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
           if (j >= len) break;
-          const float delta = bb[j] * (-a.acoef * (t.s3h * e[j]));
+          const float gj = mulc(mulc(e[j], t.s3h, t.s3h_lo), a.acoef, a.acoef_lo);
+          const float delta = a.b ? bb[j] * -gj : -mulc(gj, a.b0, a.b0_lo);
           float v = vv[j];
           if (KAHAN) {
             float cc = cs[j];
@@ -643,9 +644,9 @@ __device__ __forceinline__ void xrow(const AcXArgs<float>& a, const TileGeom& t,
       inc = pml_step_s(tabs + 4 * F, F, sl, m0, gx, a.psix, gi);
       if (a.dlt) a.dlt[gi] = bb * (ih - 0.5f * inc);
     } else {
-      inc = -a.acoef * gx;
+      inc = -mulc(gx, a.acoef, a.acoef_lo);
     }
-    const float delta = bb * inc;
+    const float delta = a.b ? bb * inc : mulc(inc, a.b0, a.b0_lo);
     float v = V[k];
     if (KAHAN) {
       float cc = SV[k];

@@ -84,6 +84,16 @@ struct Tab<double> {
   static __device__ __forceinline__ double m(const float*, const double* t64, int j) { return __ldg(t64 + j); }
 };
 
+// x times a coefficient carried as an unevaluated sum c + c_lo (c: the coefficient rounded to T; c_lo: its rounding
+// error, rounded to T; 0 in FP64), to within about one rounding of the product.  A coefficient rounded once to FP32
+// (dt, 3 / h, 1 / rho) scales every product of every step by the same factor; over thousands of steps that bias
+// becomes a phase drift of the wavefield (a relative error of about omega t times 5e-8), which the second term
+// removes.
+template <typename T>
+__device__ __forceinline__ T mulc(T x, T c, T c_lo) {
+  return fma(c_lo, x, c * x);
+}
+
 // FP32 -> FP64 widening on the integer units (IEEE 754: binary32 exponent bias 127, binary64 bias 1023, the 23
 // fraction bits become the top of the 52).  Exact for normal numbers; zero and subnormals (|f| < 1.2e-38) give 0;
 // the all-ones exponent (Inf, NaN) maps to the all-ones binary64 exponent, so a diverged field stays Inf / NaN in

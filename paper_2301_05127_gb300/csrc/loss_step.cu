@@ -68,6 +68,12 @@ static AcXArgs<T> ac_x_args(loss_ctx* h, Shot& s, const LineGeom& g, int do_B, d
   a.dt = (T)s.d.dt;
   a.acoef = (T)acoef;
   a.s3h = (T)(3.0 / s.h[2]);
+  a.dt_lo = lo_part<T>(s.d.dt);
+  a.acoef_lo = lo_part<T>(acoef);
+  a.s3h_lo = lo_part<T>(3.0 / s.h[2]);
+  a.b0_lo = lo_part<T>(s.b0);
+  a.sc = (T)(-acoef * s.b0 * (3.0 / s.h[2]));
+  a.sc_lo = lo_part<T>(-acoef * s.b0 * (3.0 / s.h[2]));
   a.minf = (T)(2.0 - std::sqrt(3.0));
   a.do_B = do_B;
   a.src.on = (do_B && s.src_on && src_amp != 0.0) ? 1 : 0;
@@ -113,6 +119,11 @@ static AcZArgs<T> ac_z_args(loss_ctx* h, Shot& s, const LineGeom& g, double acoe
   a.cv3 = (T*)s.comp[LOSS_FIELD_V3];
   a.acoef = (T)acoef;
   a.s3h = (T)(3.0 / s.h[0]);
+  a.acoef_lo = lo_part<T>(acoef);
+  a.s3h_lo = lo_part<T>(3.0 / s.h[0]);
+  a.b0_lo = lo_part<T>(s.b0);
+  a.sc = (T)(-acoef * s.b0 * (3.0 / s.h[0]));
+  a.sc_lo = lo_part<T>(-acoef * s.b0 * (3.0 / s.h[0]));
   a.minf = (T)(2.0 - std::sqrt(3.0));
   a.do_tmp = do_tmp;
   a.pml = s.pml_on ? 1 : 0;
@@ -154,6 +165,7 @@ static TileGeom tile_geom(const Shot& s, int k, int* threads, int zlogc = 4) {
   t.W = s.W[k];
   const FirConst fc = fir_const(t.M);
   t.s3h = (float)(3.0 / s.h[k]);
+  t.s3h_lo = lo_part<float>(3.0 / s.h[k]);
   t.r = (float)fc.r;
   t.a = (float)fc.a;
   t.rho = (float)fc.rho;
@@ -348,6 +360,12 @@ static ElArgs<T> el_args(const loss_ctx* h, Shot& s, int k, int pass_src, int do
   a.dt = (T)s.d.dt;
   a.acoef = (T)acoef;
   a.s3h = (T)(3.0 / s.h[k]);
+  a.dt_lo = lo_part<T>(s.d.dt);
+  a.acoef_lo = lo_part<T>(acoef);
+  a.s3h_lo = lo_part<T>(3.0 / s.h[k]);
+  a.lam0_lo = lo_part<T>(s.lam0);
+  a.mu0_lo = lo_part<T>(s.mu0);
+  a.b0_lo = lo_part<T>(s.b0);
   a.minf = (T)(2.0 - std::sqrt(3.0));
   a.do_B = do_B;
   a.do_A = do_A;

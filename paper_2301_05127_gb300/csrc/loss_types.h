@@ -68,6 +68,7 @@ struct TileGeom {
   int Rd;            // their half width, max(n_nb, K)
   int pw;            // absorbing-layer width along the axis (0 = no layer)
   float s3h, r, a, rho, inv;
+  float s3h_lo;      // rounding error of s3h (mulc)
 };
 
 // Device-side step counters of one shot, used by launches whose arguments do not change from step to step
@@ -148,6 +149,8 @@ struct AcXArgs {
   T dt;              // B step length
   T acoef;           // A step length (dt, dt/2 or -dt/2)
   T s3h;             // 3 / h_x
+  T dt_lo, acoef_lo, s3h_lo, b0_lo;  // rounding errors of dt, acoef, s3h, b0 (mulc; 0 in FP64)
+  T sc, sc_lo;       // -acoef * b0 * s3h and its rounding error (the velocity update with constant density)
   T minf;
   int do_B;
   SourceArgs src;
@@ -171,6 +174,8 @@ struct AcZArgs {
   T* cv3;
   T acoef;
   T s3h;             // 3 / h_z
+  T acoef_lo, s3h_lo, b0_lo;  // rounding errors (mulc; 0 in FP64)
+  T sc, sc_lo;       // -acoef * b0 * s3h and its rounding error
   T minf;
   int do_tmp;
   int pml;
@@ -196,6 +201,7 @@ struct ElArgs {
   const T* b;
   T lam0, mu0, b0;
   T dt, acoef, s3h, minf;
+  T dt_lo, acoef_lo, s3h_lo, lam0_lo, mu0_lo, b0_lo;  // rounding errors (mulc; 0 in FP64)
   int do_B, do_A;
   int pml;
   PmlAxis<T> pB, pA;
