@@ -542,8 +542,12 @@ loss_status_t loss_create_grid(const loss_grid_desc_t* descs, int32_t n_shots, c
 loss_status_t loss_destroy(loss_handle_t h) {
   if (!h) return LOSS_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
   drop_events(h);
   batch_destroy(h);
+  if (h->ev_x) cudaEventDestroy(h->ev_x);
+  if (h->ev_g) cudaEventDestroy(h->ev_g);
+  if (h->side) cudaStreamDestroy(h->side);
   std::vector<void*> owned = h->owned;
   for (void* p : owned) dev_free(h, p);
   cudaStreamSynchronize(h->stream);
@@ -1223,7 +1227,8 @@ bool is_velocity(int f) { return f == LOSS_FIELD_V1 || f == LOSS_FIELD_V2 || f =
 
 loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows) {
   if (s.n_rcv == 0 || rows <= s.trace_cap) return LOSS_OK;
-  const int64_t cap = std::max<int64_t>(rows, 2 * s.trace_cap);
+  // at least 256 steps of headroom, so that stepping one step at a time does not reallocate every few steps
+  const int64_t cap = std::max<int64_t>(rows + 256, 2 * s.trace_cap);
   void* nt = nullptr;
   LOSS_TRY(dev_alloc(h, (size_t)cap * s.n_rcv * s.esize, &nt));
   if (s.traces && s.rcv_steps)

@@ -152,6 +152,10 @@ struct loss_ctx {
   int64_t watch_every = 0, watch_count = 0;
   int* nflag = nullptr;
   void* stage = nullptr;  // dense device staging buffer of pinned host uploads (loss_set_field)
+  // side stream of the per-shot step's pressure / stress receiver gather, which then overlaps the z kernels:
+  // ev_x marks the end of the x kernel (the stresses are final), ev_g the end of the gather
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_x = nullptr, ev_g = nullptr;
   size_t stage_bytes = 0;
   int graph_steps = 0;   // > 0: steps are replayed from a captured CUDA graph of this many steps
   bool capturing = false;

@@ -251,8 +251,9 @@ static loss_status_t tz(loss_ctx* h, Shot& s, int mode, double acoef) {
 }
 
 template <typename T>
-static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mode) {
+static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mode, cudaStream_t st = nullptr) {
   if (s.n_rcv == 0) return LOSS_OK;
+  if (!st) st = h->stream;
   T* row = (T*)s.traces + (size_t)s.rcv_steps * s.n_rcv;
   for (int f = 0; f < LOSS_NUM_FIELDS; ++f) {
     const int64_t off = s.rcv_offsets[f], cnt = s.rcv_offsets[f + 1] - off;
@@ -262,7 +263,7 @@ static loss_status_t gather_fields(loss_ctx* h, Shot& s, bool velocities, int mo
     if (mode == 1 && s.rdelta[0])
       for (int j = 0; j < 3; ++j) d[j] = (const T*)s.rdelta[3 * f + j];
     LOSS_TRY(cuda_check(h, launch_gather<T>((const T*)s.field[f], s.rcv_idx + off, cnt, row + off, mode, d[0], d[1],
-                                            d[2], h->stream),
+                                            d[2], st),
                         "receiver gather"));
   }
   return LOSS_OK;
@@ -288,6 +289,21 @@ static loss_status_t acoustic2d_start(loss_ctx* h, Shot& s) {
   return ac_z<T, K>(h, s, 0.5 * dt, 1);
 }
 
+// The pressure receivers of a step read sigma, which is final once the x kernel has run: their gather runs on the
+// handle's side stream, overlapping the z kernels, and the main stream waits for it at the end of the step (the next
+// step's x kernel rewrites sigma).  With per-launch profiling on, everything stays on the main stream.
+static loss_status_t side_gather_begin(loss_ctx* h, bool* on) {
+  *on = !h->prof && !h->capturing;
+  if (!*on) return LOSS_OK;
+  if (!h->side) {
+    LOSS_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream"));
+    LOSS_TRY(cuda_check(h, cudaEventCreateWithFlags(&h->ev_x, cudaEventDisableTiming), "event"));
+    LOSS_TRY(cuda_check(h, cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming), "event"));
+  }
+  LOSS_TRY(cuda_check(h, cudaEventRecord(h->ev_x, h->stream), "record"));
+  return cuda_check(h, cudaStreamWaitEvent(h->side, h->ev_x, 0), "wait");
+}
+
 template <typename T, bool K>
 static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
   const double dt = s.d.dt;
@@ -297,16 +313,23 @@ static loss_status_t acoustic2d_step(loss_ctx* h, Shot& s) {
     s.staggered = true;
   }
   LOSS_TRY(gather_fields<T>(h, s, true, 0));  // v at t_{n+1/2}
-  if (sizeof(T) == 4 && tiled_ok(h, s)) {
-    LOSS_TRY(xpart<K>(h, s, 1, dt, pressure_amp(s, s.step)));
+  const bool conv = sizeof(T) == 4 && tiled_ok(h, s);
+  if (conv) LOSS_TRY(xpart<K>(h, s, 1, dt, pressure_amp(s, s.step)));
+  else LOSS_TRY((ac_x<T, K>(h, s, 1, dt, pressure_amp(s, s.step))));
+  bool side = false;
+  if (s.n_rcv) {
+    LOSS_TRY(side_gather_begin(h, &side));
+    LOSS_TRY(gather_fields<T>(h, s, false, 0, side ? h->side : h->stream));  // sigma_{n+1}
+    if (side) LOSS_TRY(cuda_check(h, cudaEventRecord(h->ev_g, h->side), "record"));
+  }
+  if (conv) {
     LOSS_TRY(tz<K>(h, s, 1, dt));
     LOSS_TRY(tz<K>(h, s, 2, 0.0));
   } else {
-    LOSS_TRY((ac_x<T, K>(h, s, 1, dt, pressure_amp(s, s.step))));
     LOSS_TRY((ac_z<T, K>(h, s, dt, 1)));
   }
   LOSS_TRY(gather_fields<T>(h, s, true, 1));   // (v_{n+1/2} + v_{n+3/2}) / 2 = v_{n+1}
-  LOSS_TRY(gather_fields<T>(h, s, false, 0));  // sigma_{n+1}
+  if (side) LOSS_TRY(cuda_check(h, cudaStreamWaitEvent(h->stream, h->ev_g, 0), "wait"));
   if (s.n_rcv) ++s.rcv_steps;
   ++s.step;
   return LOSS_OK;
