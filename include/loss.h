@@ -121,9 +121,19 @@ loss_status_t loss_destroy(loss_handle_t handle);
 /* Set the model of one shot from dense double arrays of the grid shape: P velocity vp, S velocity vs
  * (elastic only; pass NULL for acoustic grids) and density rho.  Stored as kappa = rho vp^2 and b = 1/rho
  * (acoustic) or lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2, b = 1/rho (elastic), paper Sec. 2.
- * Arrays are copied.  LOSS_E_ARG if rho <= 0 anywhere or a required pointer is NULL. */
+ * Arrays are copied.  FP32 grids store these coefficients with loss_round_fp32_unbiased (key = 3 i + m for
+ * point i of coefficient array m), so that a region of constant coefficients carries no common rounding bias.
+ * LOSS_E_ARG if rho <= 0 anywhere or a required pointer is NULL. */
 loss_status_t loss_set_model(loss_handle_t handle, int32_t shot, const double* vp, const double* vs,
                              const double* rho, int32_t mem);
+
+/* Host-side conversion of n doubles to FP32 by unbiased (stochastic) rounding: a value that FP32 does not
+ * hold exactly becomes one of its two FP32 neighbours lo < x < hi, hi with probability (x - lo) / (hi - lo),
+ * so that the expected result is x.  The uniform variate of element i is the top 53 bits of the SplitMix64
+ * output (Steele, Lea and Flood, OOPSLA 2014) for the input key0 + i, scaled to [0, 1): the conversion is
+ * deterministic.  Values FP32 holds exactly, and non-finite values, convert as by a cast.  Needs no GPU and no
+ * handle.  LOSS_E_ARG if n < 0 or a pointer is NULL while n > 0. */
+loss_status_t loss_round_fp32_unbiased(const double* x, float* out, int64_t n, uint64_t key0);
 
 /* Ricker source f_r(t) = (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 (paper Sec. 4.2), with the Gaussian
  * spatial amplitude of Sec. 4.2: exp(-|o|^2 / 8) over integer offsets o (standard deviation 2 cells per

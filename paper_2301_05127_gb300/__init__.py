@@ -88,6 +88,7 @@ _PROTOS = {
     "loss_set_wait_limit": (_I32, [_H, _I64]),
     "loss_set_watchdog": (_I32, [_H, _I64]),
     "loss_set_coordinates": (_I32, [_H, _I32, _I32, _P]),
+    "loss_round_fp32_unbiased": (_I32, [_P, _P, _I64, ctypes.c_uint64]),
 }
 KERNELS = {"acoustic_x": 0, "acoustic_z": 1, "gather": 2, "derivative": 3, "elastic_x": 4, "elastic_y": 5,
            "elastic_z": 6, "clock": 7, "adjoint": 8, "acoustic_x2": 9, "acoustic_z2": 10, "watch": 11}
@@ -143,6 +144,15 @@ def make_desc(dim, physics, precision, n_nb, n, p, h, dt) -> GridDesc:
         d.n[i], d.p[i], d.h[i] = int(nn[i]), int(pp[i]), float(hh[i])
     d.dt = float(dt)
     return d
+
+
+def round_fp32_unbiased(x, key0: int = 0) -> np.ndarray:
+    """loss_round_fp32_unbiased: x (float64) to FP32 by deterministic unbiased rounding, as FP32 grids store
+    their model coefficients (element i uses the key key0 + i)."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(a.shape, dtype=np.float32)
+    _check(lib().loss_round_fp32_unbiased(a.ctypes.data, out.ctypes.data, a.size, int(key0)))
+    return out
 
 
 class _TorchAllocator:

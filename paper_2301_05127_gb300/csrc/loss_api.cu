@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 #include <vector>
@@ -780,6 +781,33 @@ static loss_status_t get_shot(loss_ctx* h, int32_t shot, Shot** s) {
   return LOSS_OK;
 }
 
+// SplitMix64 output function for input z (Steele, Lea and Flood, OOPSLA 2014): a bijective 64-bit mix.
+static inline uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// x rounded to one of its two FP32 neighbours with probabilities that make the result unbiased.
+static float round_unbiased(double x, uint64_t key) {
+  const float f = (float)x;
+  const double d = (double)f;
+  if (d == x || !std::isfinite(f) || !std::isfinite(x)) return f;
+  const float g = std::nextafter(f, d < x ? std::numeric_limits<float>::infinity()
+                                          : -std::numeric_limits<float>::infinity());
+  const double lo = std::min(d, (double)g), hi = std::max(d, (double)g);
+  const double up = (x - lo) / (hi - lo);
+  const double u = (double)(splitmix64(key) >> 11) * 0x1.0p-53;
+  return (float)(u < up ? hi : lo);
+}
+
+loss_status_t loss_round_fp32_unbiased(const double* x, float* out, int64_t n, uint64_t key0) {
+  if (n < 0 || (n > 0 && (!x || !out))) return LOSS_E_ARG;
+  for (int64_t i = 0; i < n; ++i) out[i] = round_unbiased(x[i], key0 + (uint64_t)i);
+  return LOSS_OK;
+}
+
 loss_status_t loss_set_model(loss_handle_t h, int32_t shot, const double* vp, const double* vs, const double* rho,
                              int32_t mem) {
   Shot* s;
@@ -839,7 +867,9 @@ loss_status_t loss_set_model(loss_handle_t h, int32_t shot, const double* vp, co
       LOSS_TRY(copy_in(h, *s, s->model[m], md[m].data(), LOSS_MEM_HOST));
     } else {
       std::vector<float> f(N);
-      for (int64_t i = 0; i < N; ++i) f[i] = (float)md[m][i];
+      // unbiased rounding: a layer of constant kappa (or lambda, mu) would otherwise carry one common relative
+      // error of up to 2^-24, a systematic wave-speed bias whose phase error grows with the travel time
+      for (int64_t i = 0; i < N; ++i) f[i] = round_unbiased(md[m][i], 3 * (uint64_t)i + (uint64_t)m);
       LOSS_TRY(copy_in(h, *s, s->model[m], f.data(), LOSS_MEM_HOST));
       LOSS_TRY(cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
     }

@@ -5,14 +5,20 @@ Each workload runs over its whole length on the GPU, in the launch configuration
 compared with the oracle element by element:
 
 * receiver traces after every step: max |gpu - ref| over the run / max |ref| over the run, per field;
-* every field at four checkpoints, sampled on a regular sub-grid: ||gpu - ref||_2 / (largest ||ref||_2 over the
-  checkpoints), per field (the run error of the paper's normalisation by the reference maximum, Sec. 4), and
-  element by element, max |gpu - ref| / max |ref| over the run, so that a defect confined to a few points (one
-  tile's edge, one patch) cannot hide in the norm;
+* every field at four checkpoints, sampled on a regular sub-grid, on the physical domain (the points outside
+  the absorbing layers): ||gpu - ref||_2 / (largest ||ref||_2 over the checkpoints), per field (the run error of
+  the paper's normalisation by the reference maximum, Sec. 4), and element by element, max |gpu - ref| /
+  max |ref| over the run, so that a defect confined to a few points (one tile's edge, one patch) cannot hide in
+  the norm;
+* the same L2 error over the whole sampled grid, absorbing layers included;
 * the full-field L2 norms at the checkpoints, relative to the largest norm of the run.
 
 Tolerances: 1e-12 for the FP64 path, 1e-5 for the FP32 forms (FP32 fields, FP32 with compensated updates); the
-element-wise field bound is ten times those (a maximum over many points of a rounding-level difference)."""
+element-wise field bound is ten times those (a maximum over many points of a rounding-level difference).  The
+whole-grid error is held to ten times the tolerance: on the outermost row of an absorbing layer the damping
+profile's alpha vanishes, every static field profile there is an equilibrium of the layer's equations, and
+rounding differences accumulate undamped (two FP64 implementations that differ only in the rounding order of
+the layer update differ there by about a thousand times their difference elsewhere)."""
 import dataclasses
 import importlib.util
 import os
@@ -25,6 +31,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32_kahan": 1e-5}
 POINT = 10.0  # element-wise field errors: POINT * TOL
+LAYERS = 10.0  # whole-grid field errors, absorbing layers included: LAYERS * TOL
 
 
 def _golden_module():
@@ -53,16 +60,24 @@ def _load(name):
     return dict(np.load(path))
 
 
-def _errors(gold, fields, snaps, norms, traces):
-    """Relative errors per field of the GPU run against the golden run."""
+def _inner(shape, stride, width):
+    """Slices of the sampled grid (stride `stride`) that keep the points outside absorbing layers `width` wide."""
+    return tuple(slice(-(-width // stride), (n - 1 - width) // stride + 1) for n in shape)
+
+
+def _errors(gold, fields, snaps, norms, traces, inner):
+    """Relative errors per field of the GPU run against the golden run; `inner` selects the physical domain of
+    the sampled grid."""
     errs = {}
     for f in fields:
         ref = gold[f"snap_{f}"]
-        peak = max(float(np.linalg.norm(r)) for r in ref)
+        peak = max(float(np.linalg.norm(r[inner])) for r in ref)
         if peak > 0:
-            errs[f"snap_{f}"] = max(float(np.linalg.norm(a - r)) for a, r in zip(snaps[f], ref)) / peak
-            amax = max(float(np.abs(r).max()) for r in ref)
-            errs[f"point_{f}"] = max(float(np.abs(a - r).max()) for a, r in zip(snaps[f], ref)) / amax / POINT
+            errs[f"snap_{f}"] = max(float(np.linalg.norm((a - r)[inner])) for a, r in zip(snaps[f], ref)) / peak
+            amax = max(float(np.abs(r[inner]).max()) for r in ref)
+            errs[f"point_{f}"] = max(float(np.abs((a - r)[inner]).max()) for a, r in zip(snaps[f], ref)) / amax / POINT
+            whole = max(float(np.linalg.norm(r)) for r in ref)
+            errs[f"layers_{f}"] = max(float(np.linalg.norm(a - r)) for a, r in zip(snaps[f], ref)) / whole / LAYERS
         nref = gold[f"norm_{f}"]
         if nref.max() > 0:
             errs[f"norm_{f}"] = float(np.abs(np.asarray(norms[f]) - nref).max() / nref.max())
@@ -101,7 +116,7 @@ def _single(pkg, name, prec, fields, family=None):
     rec = g.record(0)
     traces = {f: rec[f].astype(np.float64) for f in w.receivers}
     g.close()
-    errs = _errors(gold, fields, snaps[0], norms[0], traces)
+    errs = _errors(gold, fields, snaps[0], norms[0], traces, _inner(g.shape(0), stride, w.pml_width))
     _report(f"{name} {prec}{'/' + family if family else ''}", errs)
     return errs
 
@@ -109,7 +124,7 @@ def _single(pkg, name, prec, fields, family=None):
 def _report(label, errs):
     worst = lambda key: max((v for k, v in errs.items() if k.startswith(key)), default=0.0)  # noqa: E731
     print(f"[full run] {label}: fields {worst('snap'):.2e}, points {POINT * worst('point'):.2e}, "
-          f"norms {worst('norm'):.2e}, traces {worst('trace'):.2e}")
+          f"whole grid {LAYERS * worst('layers'):.2e}, norms {worst('norm'):.2e}, traces {worst('trace'):.2e}")
 
 
 ACOUSTIC = ("sigma", "v1", "v3")
@@ -184,7 +199,8 @@ def test_survey_full_run(pkg, prec, graph):
     worst = {}
     for s in picks:
         rec = g.record(idx[s])
-        errs = _errors(gold[s], ACOUSTIC, snaps[idx[s]], norms[idx[s]], {"sigma": rec["sigma"].astype(np.float64)})
+        errs = _errors(gold[s], ACOUSTIC, snaps[idx[s]], norms[idx[s]], {"sigma": rec["sigma"].astype(np.float64)},
+                       _inner(g.shape(idx[s]), stride[s], ws[s].pml_width))
         _report(f"survey shot {s} ({ws[s].n[0]}^2) {prec}", errs)
         worst[s] = max(errs.values())
         assert worst[s] < TOL[prec], (s, errs)
