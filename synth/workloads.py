@@ -82,6 +82,12 @@ def _top_row_receivers(shape) -> np.ndarray:
     return np.arange(int(np.prod(shape[1:])), dtype=np.int64)
 
 
+def _row_receivers(shape, z: int) -> np.ndarray:
+    """Flat indices of every point on the plane of axis-0 index z."""
+    plane = int(np.prod(shape[1:]))
+    return z * plane + np.arange(plane, dtype=np.int64)
+
+
 def acoustic2d_small(n: int = 128, p: int = 2, steps: int = 300, n_nb: int = 12, pml_width: int = 20) -> Workload:
     """2-D acoustic, constant v = 2000 m/s, rho = 1000 kg/m^3, h = 10 m, Ricker 15 Hz at the centre, FP64, with
     an absorbing ADE-PML layer of ``pml_width`` points on every side."""
@@ -151,7 +157,9 @@ def elastic3d_heterogeneous(n: int = 192, p: int = 4, steps: int = 1500, n_nb: i
                             precision: str = "fp32_kahan", seeds=(4001, 4002, 4003),
                             true_model: bool = True, pml_width: int = 20) -> Workload:
     """3-D elastic with smooth random vp/vs/rho (5 %, 100 m correlation length, clipped so vp/vs >= 1.5).
-    ``true_model=False`` gives the homogeneous starting model of the inversion."""
+    ``true_model=False`` gives the homogeneous starting model of the inversion.  The v3 receivers cover the plane
+    z = pml_width, the top of the physical domain: the adjoint run injects its sources there, and on the
+    outermost plane of an absorbing layer (z = 0) rounding differences accumulate undamped."""
     shape = (n + 1,) * 3
     h = 10.0
     corr = 100.0 / h
@@ -171,7 +179,7 @@ def elastic3d_heterogeneous(n: int = 192, p: int = 4, steps: int = 1500, n_nb: i
         name=f"elastic3d_hetero_{n}_p{p}", dim=3, physics="elastic", n=(n,) * 3, p=(p,) * 3, h=(h,) * 3,
         n_nb=n_nb, dt=_cfl_dt(h, vmax), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
         src_kinds=("explosive", "shear_xz"), f0=f0, t0=1.2 / f0,
-        receivers={"v3": _top_row_receivers(shape)}, precision=precision,
+        receivers={"v3": _row_receivers(shape, pml_width)}, precision=precision,
         checkpoint_every=int(math.ceil(math.sqrt(steps))), seed=seeds[0], pml_width=pml_width)
 
 
@@ -179,11 +187,15 @@ def batched_shots(n_shots: int = 64, steps: int = 1500, n_nb: int = 20, seed: in
                   sizes=tuple(range(512, 2049, 128)), M: int = 128, precision: str = "fp32"):
     """Shots of a 2-D acoustic survey with uneven square grids: n_s drawn uniformly from ``sizes`` (multiples
     of M), p_s = n_s / M patches per axis, 3-5 horizontal layers with v ~ U[1500, 4000] sorted by depth,
-    rho = 1000, Ricker 20 Hz at (z = 5, x = n_s / 2)."""
+    rho = 1000, absorbing layers of 40 points on every side.  Source and receivers lie at the top of the physical
+    domain, just below the upper layer: a Ricker 20 Hz at (z = 45, x = n_s / 2), receivers on the row z = 40.
+    (Inside an absorbing layer the fields are not physical, and its outermost row carries a slowly decaying
+    residual whose update is a near-cancellation between the memory variable and the derivative it balances.)"""
     rng = np.random.default_rng(seed)
     ns = rng.choice(np.asarray(sizes), size=n_shots)
     out = []
     h = 10.0
+    pml = 40
     for s, n in enumerate(ns):
         n = int(n)
         r = np.random.default_rng(seed + 1 + s)
@@ -201,9 +213,9 @@ def batched_shots(n_shots: int = 64, steps: int = 1500, n_nb: int = 20, seed: in
         out.append(Workload(
             name=f"shot{s}_{n}", dim=2, physics="acoustic", n=(n, n), p=(n // M, n // M), h=(h, h),
             n_nb=n_nb, dt=_cfl_dt(h, float(v_layers.max())), steps=steps, model_fn=model,
-            src_index=(5, n // 2), src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
-            receivers={"sigma": _top_row_receivers(shape)}, precision=precision, seed=seed + 1 + s,
-            pml_width=40))
+            src_index=(pml + 5, n // 2), src_kinds=("pressure",), f0=f0, t0=1.2 / f0,
+            receivers={"sigma": _row_receivers(shape, pml)}, precision=precision, seed=seed + 1 + s,
+            pml_width=pml))
     return out
 
 

@@ -11,8 +11,10 @@ for one workload run over its whole length:
   [checkpoints, *sampled shape]);
 * ``norm_<field>``: the full-field L2 norm of every field at the checkpoints.
 
-The receivers sit where the wavefield is: lines through the source (2-D) or lines on the top plane (3-D), 33
-points each; the workloads' own receiver sets are whole planes or rows and too large to store for every step.
+The receivers sit where the wavefield is: lines through the source (2-D; for the survey shots the receiver row and
+the source column) or lines on the receiver plane (3-D: z = 0 for the homogeneous run, the top of the physical
+domain for the heterogeneous one), 33 points each; the workloads' own receiver sets are whole planes or rows and too
+large to store for every step.
 
 Usage: python tests/golden/make_full_runs.py [name ...]     (default: every name of golden_names(); the 3-D runs
 take hours of CPU time on 8 cores)
@@ -48,13 +50,13 @@ def _rcv_2d_through_source(w) -> np.ndarray:
     return np.unique(np.concatenate([row, col])).astype(np.int64)
 
 
-def _rcv_top_plane_lines(w) -> np.ndarray:
-    """33 points along x and 33 along y on the plane z = 0, through the source's (y, x)."""
+def _rcv_plane_lines(w, z: int = 0) -> np.ndarray:
+    """33 points along x and 33 along y on the plane of axis-0 index z, through the source's (y, x)."""
     _, ny, nx = w.n
     _, ys, xs = w.src_index
     a = ys * (nx + 1) + _line_points(nx)
     b = _line_points(ny) * (nx + 1) + xs
-    return np.unique(np.concatenate([a, b])).astype(np.int64)
+    return (z * (ny + 1) * (nx + 1) + np.unique(np.concatenate([a, b]))).astype(np.int64)
 
 
 def survey_shot_indices(shots) -> tuple:
@@ -81,16 +83,16 @@ def golden_workload(name: str):
         return dataclasses.replace(w, receivers={"sigma": _rcv_2d_through_source(w)}), 16
     if name == "elastic3d_homogeneous":
         w = W.elastic3d_homogeneous(precision="fp64")
-        r = _rcv_top_plane_lines(w)
+        r = _rcv_plane_lines(w)
         return dataclasses.replace(w, receivers={"v1": r, "v2": r, "v3": r}), 16
     if name == "elastic3d_heterogeneous":
         w = W.elastic3d_heterogeneous(precision="fp64")
-        return dataclasses.replace(w, receivers={"v3": _rcv_top_plane_lines(w)}), 12
+        return dataclasses.replace(w, receivers={"v3": _rcv_plane_lines(w, w.pml_width)}), 12
     if name.startswith("survey_shot"):
         s = int(name[len("survey_shot"):])
         w = W.batched_shots()[s]
         nz, nx = w.n
-        row = _line_points(nx)  # the top row z = 0
+        row = w.pml_width * (nx + 1) + _line_points(nx)  # the receiver row, the top of the physical domain
         col = _line_points(nz) * (nx + 1) + w.src_index[1]
         return dataclasses.replace(w, receivers={"sigma": np.unique(np.concatenate([row, col]))}), 32
     raise KeyError(name)

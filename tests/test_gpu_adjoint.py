@@ -174,3 +174,34 @@ def test_heterogeneous_elastic_full_geometry(pkg):
         assert np.isfinite(g32[k]).all()
         err = np.abs(g32[k] - g64[k]).max() / np.abs(g64[k]).max()
         assert err < 1e-2, (k, err)
+
+
+def test_heterogeneous_elastic_gradient_over_the_whole_run(pkg):
+    """The gradient workload over its whole length: 193^3 points, 1500 steps, checkpoints every ceil(sqrt(1500))
+    = 39 steps.  Data from the heterogeneous model (FP64), gradient at the homogeneous start model in FP32 with
+    compensated updates against the FP64 GPU form (itself matched to the oracle's adjoint on the smaller cases
+    above): misfit within 1e-3, each gradient within 1e-3 in L2 and 1e-2 point by point, relative to its largest
+    value."""
+    steps = 1500
+    true = elastic3d_heterogeneous(steps=steps)
+    start = elastic3d_heterogeneous(steps=steps, true_model=False)
+    g = pkg.Grid.from_workloads([dataclasses.replace(true, precision="fp64")])
+    g.step(steps)
+    obs = g.record(0)["_all"].astype(np.float64)
+    g.close()
+    res = {}
+    for prec in ("fp32_kahan", "fp64"):
+        g = pkg.Grid.from_workloads([dataclasses.replace(start, precision=prec)])
+        res[prec] = g.gradient(0, obs, steps)
+        g.close()
+    J32, g32 = res["fp32_kahan"]
+    J64, g64 = res["fp64"]
+    report = {"misfit": abs(J32 - J64) / J64}
+    for k in ("vp", "vs", "rho"):
+        assert np.isfinite(g32[k]).all()
+        report[f"{k} L2"] = float(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k]))
+        report[f"{k} max"] = float(np.abs(g32[k] - g64[k]).max() / np.abs(g64[k]).max())
+    print("[gradient 193^3 x 1500]", {k: f"{v:.2e}" for k, v in report.items()})
+    assert J64 > 0 and report["misfit"] <= 1e-3, report
+    for k in ("vp", "vs", "rho"):
+        assert report[f"{k} L2"] < 1e-3 and report[f"{k} max"] < 1e-2, report
