@@ -180,8 +180,10 @@ def test_heterogeneous_elastic_gradient_over_the_whole_run(pkg):
     """The gradient workload over its whole length: 193^3 points, 1500 steps, checkpoints every ceil(sqrt(1500))
     = 39 steps.  Data from the heterogeneous model (FP64), gradient at the homogeneous start model in FP32 with
     compensated updates against the FP64 GPU form (itself matched to the oracle's adjoint on the smaller cases
-    above): misfit within 1e-3, each gradient within 1e-3 in L2 and 1e-2 point by point, relative to its largest
-    value."""
+    above): the misfit and each gradient, in L2 and point by point relative to its largest value, within the FP32
+    tolerance of 1e-5 over the run (measured: 6.3e-7 for the misfit, at most 6.6e-6 for the gradients).  The
+    receivers lie on the top plane of the physical domain; on the outermost plane of the absorbing layer, where
+    the adjoint sources would act on undamped rounding modes, the same comparison gave 2.2e-3."""
     steps = 1500
     true = elastic3d_heterogeneous(steps=steps)
     start = elastic3d_heterogeneous(steps=steps, true_model=False)
@@ -202,6 +204,6 @@ def test_heterogeneous_elastic_gradient_over_the_whole_run(pkg):
         report[f"{k} L2"] = float(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k]))
         report[f"{k} max"] = float(np.abs(g32[k] - g64[k]).max() / np.abs(g64[k]).max())
     print("[gradient 193^3 x 1500]", {k: f"{v:.2e}" for k, v in report.items()})
-    assert J64 > 0 and report["misfit"] <= 1e-3, report
+    assert J64 > 0 and report["misfit"] <= 1e-5, report
     for k in ("vp", "vs", "rho"):
-        assert report[f"{k} L2"] < 1e-3 and report[f"{k} max"] < 1e-2, report
+        assert report[f"{k} L2"] < 1e-5 and report[f"{k} max"] < 1e-5, report
