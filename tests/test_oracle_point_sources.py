@@ -17,8 +17,10 @@ buoyancy, force timing or sign would show as several percent or more.
 The explosive source adds s(t) A(x) to the rate of each normal stress (s = amp f_r).  With S the time integral of
 s, that is the body force S(t) grad A.  Its field is the gradient of a P potential phi with phi_tt - alpha^2
 Laplacian phi = S A / rho, so v = grad sum_k A_k h^3 s(t - r_k / alpha) / (4 pi rho alpha^2 r_k): radial, with no S
-wave.  It agrees to about 0.2-0.3 % of the peak, and the components an S wave would carry stay at rounding
-level.
+wave.  It agrees to about 0.2-0.3 % of the peak.  At the three receivers on symmetry axes and planes of the grid
+and source (along z, along x, on the x = z diagonal) the velocity components across the source-receiver
+direction, which an S wave would carry, stay at rounding level (below 1e-10 of the peak); a source that broke the
+isotropy of the three normal stresses would put them at the P wave's order there.
 
 The shear source adds s A to the rate of sigma13 (x-z).  That is the body force S (d_z A, 0, d_x A), a double
 couple, whose velocity is sum_k A_k h^3 (d_z U^(x) + d_x U^(z)), where U^(j) is Stokes' displacement for a force of
@@ -160,6 +162,11 @@ def test_explosive_source_radiates_the_exact_p_field():
         exact = np.array([_explosion_velocity(dx, A, t, vp, rho, w.f0, w.t0, w.amp) for t in times])
         err = np.abs(np.array(traces[r]) - exact).max() / np.abs(exact).max()
         assert err < 1e-2, (r, err)
+        if r != (-6, 5, 4):  # on a symmetry axis or plane: no transverse motion
+            v = np.array(traces[r])
+            g = np.array(r, dtype=np.float64) / np.linalg.norm(r)
+            across = v - (v @ g)[:, None] * g[None, :]
+            assert np.abs(across).max() < 1e-10 * np.abs(v).max(), (r, np.abs(across).max() / np.abs(v).max())
 
 
 def test_shear_source_radiates_the_exact_double_couple_field():
