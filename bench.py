@@ -266,6 +266,28 @@ def _batched_leg(torch, pkg, units, warmup_units, k):
             "autotune": tune, "launches": launches, "l2": "working set 4.5 GB, no flush"}
 
 
+# GB300's FP64 FMA rate, from its unit counts and clock: 152 SMs x 2 DFMA per clock x 2.07 GHz (1.26 TFLOP/s, the
+# nominal 1.25 TFLOP/s of the part).
+FP64_DFMA_PER_S = 152 * 2 * 2.07e9
+
+
+def _junction_taps(n, c, radius):
+    """FP64 FMAs of one junction sum at position c of an n-interval line (taps m in [-radius, radius], clipped to
+    the line)."""
+    return min(radius, c) + min(radius, n - c) + 1
+
+
+def elastic_dfma_per_point_step(n, p, n_nb, K=16):
+    """FP64 FMAs per point-step of the FP32 elastic step on an n^3 grid with p patches per axis: the x passes sum
+    every junction of a line once for each of their 6 derivatives (PMBC sums, radius n_nb); the y / z tiles sum
+    both junctions of their patch for each of their 12 derivatives (junction corrections, radius max(n_nb, K))."""
+    M = n // p
+    line = sum(_junction_taps(n, j * M, n_nb) for j in range(p + 1))
+    rd = max(n_nb, K)
+    tiles = sum(_junction_taps(n, l * M, rd) + _junction_taps(n, (l + 1) * M, rd) for l in range(p))
+    return (6 * line + 12 * tiles) / (n + 1)
+
+
 def _elastic_leg(torch, pkg, steps, warmup, flush):
     """The homogeneous 3-D elastic workload (257^3 points, 4 x 4 x 4 patches, n_nb = 20, 20-point layers,
     explosive + shear source, v1..v3 receivers on z = 0), FP32 with compensated updates, tile shapes from the
@@ -289,8 +311,14 @@ def _elastic_leg(torch, pkg, steps, warmup, flush):
     # Derivative temporaries are not algorithmic.
     alg, alg_comp = ELASTIC_ALG_BYTES, 2 * ELASTIC_ALG_BYTES
     value = w.points / (ms_step * 1e-3)
+    # The PMBC sums stay in FP64, and GB300's FP64 rate is low: their FMAs set a floor above the HBM one.
+    dfma = elastic_dfma_per_point_step(w.n[0], w.p[0], w.n_nb)
+    fp64_floor_ms = 1e3 * w.points * dfma / FP64_DFMA_PER_S
     return {"workload": "elastic3d_homogeneous 257^3 pts, 4x4x4 patches (M=64), n_nb=20, PML 20, FP32 + Kahan",
             "value": value, "unit": UNIT, "ms_per_step": ms_step,
+            "fp64": {"bound": "alu", "dfma_per_point_step": dfma, "floor_ms": fp64_floor_ms,
+                     "frac": fp64_floor_ms / ms_step, "peak_tflops": 2e-12 * FP64_DFMA_PER_S,
+                     "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2.07 GHz"},
             "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items()},
             "alg_bytes_per_point": alg, "alg_frac_of_peak": value * alg / (peak * 1e9),
             "alg_bytes_per_point_with_compensation": alg_comp,

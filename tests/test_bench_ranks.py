@@ -58,3 +58,14 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.run_reference(argparse.Namespace(steps=1, warmup=3)) is None
+
+
+def test_elastic_fp64_count_by_hand():
+    """FP64 FMAs per point-step of the elastic step, counted by hand for 257 points per axis, 4 patches (M = 64),
+    n_nb = 20: an x line sums junctions of 21, 41, 41, 41, 21 taps (165) for 6 derivatives; a y / z line's tiles
+    sum (21 + 41) + (41 + 41) + (41 + 41) + (41 + 21) = 288 taps for 12 derivatives."""
+    import bench
+
+    assert abs(bench.elastic_dfma_per_point_step(256, 4, 20) - (6 * 165 + 12 * 288) / 257) < 1e-12
+    # one patch per axis: only the two end junctions, one-sided
+    assert abs(bench.elastic_dfma_per_point_step(64, 1, 8) - (6 * 18 + 12 * 34) / 65) < 1e-12
