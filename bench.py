@@ -290,7 +290,7 @@ def elastic_dfma_per_point_step(n, p, n_nb, K=16):
 
 def _elastic_leg(torch, pkg, steps, warmup, flush):
     """The homogeneous 3-D elastic workload (257^3 points, 4 x 4 x 4 patches, n_nb = 20, 20-point layers,
-    explosive + shear source, v1..v3 receivers on z = 0), FP32 with compensated updates, tile shapes from the
+    explosive + shear source, v1..v3 receivers on z = 20), FP32 with compensated updates, tile shapes from the
     library's autotuner, per-step events with an L2 flush in between; per-kernel times from the library's
     events."""
     from synth import elastic3d_homogeneous

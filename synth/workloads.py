@@ -137,7 +137,8 @@ def acoustic2d_layered(n: int = 2048, p: int = 8, steps: int = 2000, n_nb: int =
 def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int = 20,
                           precision: str = "fp32_kahan", pml_width: int = 20) -> Workload:
     """3-D isotropic elastic, vp = 3000, vs = 1730, rho = 2000, explosive plus shear source at the centre,
-    15 Hz Ricker, receivers v1, v2, v3 on the top plane."""
+    15 Hz Ricker, receivers v1, v2, v3 on the top plane of the physical domain (z = pml_width; on the outermost
+    plane of the absorbing layer the field is an attenuated remnant carrying undamped rounding modes)."""
     shape = (n + 1,) * 3
     h = 10.0
 
@@ -145,7 +146,7 @@ def elastic3d_homogeneous(n: int = 256, p: int = 4, steps: int = 1000, n_nb: int
         return np.full(shape, 3000.0), np.full(shape, 1730.0), np.full(shape, 2000.0)
 
     f0 = 15.0
-    top = _top_row_receivers(shape)
+    top = _row_receivers(shape, pml_width)
     return Workload(
         name=f"elastic3d_homog_{n}_p{p}", dim=3, physics="elastic", n=(n,) * 3, p=(p,) * 3, h=(h,) * 3,
         n_nb=n_nb, dt=_cfl_dt(h, 3000.0), steps=steps, model_fn=model, src_index=(n // 2,) * 3,
