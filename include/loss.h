@@ -270,9 +270,11 @@ loss_status_t loss_set_schedule(loss_handle_t handle, int32_t batched, int32_t g
  * LOSS_KERNELS_CONVOLUTION (the default) = the truncated-convolution form: the same patch systems solved through
  * the closed-form inverse of the (1, 4, 1) operator, truncated where |sqrt(3) - 2|^k < 1e-9, with exact patch-end
  * corrections from the PMBC junction values (x rows pipelined through TMA bulk copies, z lines on independent
- * 32-column x one-patch tiles).  Both agree with the FP64 oracle at the FP32 tolerance; they differ in rounding.
- * LOSS_E_ARG for another value. */
-enum { LOSS_KERNELS_LINE = 0, LOSS_KERNELS_CONVOLUTION = 1 };
+ * 32-column x one-patch tiles; rows the pipelined kernel does not take, longer than 2049 points or with patches
+ * whose length is not a multiple of 8, go to independent (row, patch) items in two launches);
+ * LOSS_KERNELS_CONVOLUTION_ITEMS = the same with every row on (row, patch) items.  All agree with the FP64 oracle
+ * at the FP32 tolerance; they differ in rounding.  LOSS_E_ARG for another value. */
+enum { LOSS_KERNELS_LINE = 0, LOSS_KERNELS_CONVOLUTION = 1, LOSS_KERNELS_CONVOLUTION_ITEMS = 2 };
 loss_status_t loss_set_kernels(loss_handle_t handle, int32_t family);
 
 /* One autotuner result: the tile shape chosen for a kernel family and its measured mean launch time. */

@@ -387,8 +387,10 @@ class Grid:
         _check(lib().loss_set_tile(self.h, kid, int(threads_per_block), int(chunk_log2)), self.h)
 
     def set_kernels(self, family: str = "convolution"):
-        """Kernel family of the per-shot FP32 2-D acoustic step: "line" or "convolution" (loss_set_kernels)."""
-        _check(lib().loss_set_kernels(self.h, {"line": 0, "convolution": 1}[family]), self.h)
+        """Kernel family of the per-shot FP32 2-D acoustic step: "line", "convolution" or "convolution_items"
+        (loss_set_kernels)."""
+        _check(lib().loss_set_kernels(self.h, {"line": 0, "convolution": 1, "convolution_items": 2}[family]),
+               self.h)
 
     def set_schedule(self, batched: bool = True, graph_steps: int = 0):
         _check(lib().loss_set_schedule(self.h, 1 if batched else 0, int(graph_steps)), self.h)

@@ -580,7 +580,7 @@ loss_status_t loss_set_tile(loss_handle_t h, int32_t kernel, int32_t threads_per
 
 loss_status_t loss_set_kernels(loss_handle_t h, int32_t family) {
   LOSS_TRY(guard(h));
-  if (family != LOSS_KERNELS_LINE && family != LOSS_KERNELS_CONVOLUTION)
+  if (family != LOSS_KERNELS_LINE && family != LOSS_KERNELS_CONVOLUTION && family != LOSS_KERNELS_CONVOLUTION_ITEMS)
     return fail(h, LOSS_E_ARG, "unknown kernel family");
   for (const Shot& s : h->shots)
     if (s.staggered) return fail(h, LOSS_E_STATE, "choose the kernel family before the first step");

@@ -144,7 +144,7 @@ struct loss_ctx {
   int tile_threads[LOSS_NUM_KERNELS] = {};     // 0 = built-in choice (loss_set_tile)
   // schedule (loss_set_schedule)
   int batched = 1;       // several 2-D acoustic shots: one persistent launch per kernel over all of them
-  int tiled = 1;         // FP32 2-D acoustic shots stepped one at a time: truncated-convolution tile kernels
+  int tiled = 1;         // LOSS_KERNELS_* family of the FP32 2-D acoustic shots stepped one at a time
   int* dflag = nullptr;  // device error flag of kernels with bounded waits (read by loss_sync)
   unsigned wait_polls = 1u << 24;  // poll limit of those waits (loss_set_wait_limit)
   // non-finite watchdog (loss_set_watchdog): every watch_every steps (0 = off) a check of every field sets nflag to
@@ -263,6 +263,10 @@ template <bool KAHAN>
 cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagic, int* err, unsigned polls,
                       int num_sms, cudaStream_t st);
 size_t tile_smem_z(const TileGeom& t, int mode, int logc);
+// loss_kernels_xtile.cu: the x part on (row, x patch) items, for rows the pipelined x kernel does not take
+template <bool KAHAN>
+cudaError_t launch_xt(const AcXArgs<float>& a, const TileGeom& t, cudaStream_t st);
+size_t xt_smem(const TileGeom& t);
 // loss_kernels_elastic.cu: elastic y / z tile passes (FP32)
 size_t elt_smem(const ElTile& g, int logc);
 template <bool KAHAN>

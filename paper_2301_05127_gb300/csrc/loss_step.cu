@@ -205,26 +205,30 @@ static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
 // The pipelined x kernel takes rows of at most 2048 points in at most 64 patches whose length is a multiple of 8,
 // with the staged rows within shared memory.
 static bool xp_ok(const loss_ctx* h, const Shot& s, const TileGeom& t) {
-  return s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 &&
+  return h->tiled != LOSS_KERNELS_CONVOLUTION_ITEMS && s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 &&
          xp_smem(t, s.kahan) + 2048 <= (size_t)h->smem_optin;
 }
 
 // x part of the FP32 step (sub-step B and the x part of A, or the latter alone): the pipelined row kernel when a
-// row fits one block, else the line kernel.
+// row fits its shared-memory stages, else the (row, patch) item kernels, two launches.
 template <bool K>
 static loss_status_t xpart(loss_ctx* h, Shot& s, int do_B, double acoef, double amp) {
   int threads;
   TileGeom t = tile_geom(s, 2, &threads);
+  LOSS_TRY(ensure_delta_weights(h, s, 2));
+  t.Wd = s.Wd[2];
+  t.ncross = (int)s.len[0];
+  const AcXArgs<float> a = ac_x_args<float>(h, s, LineGeom{}, do_B, acoef, amp);
+  LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
   if (xp_ok(h, s, t)) {
-    LOSS_TRY(ensure_delta_weights(h, s, 2));
-    t.Wd = s.Wd[2];
-    t.ncross = (int)s.len[0];
     const unsigned mm = (unsigned)((((uint64_t)1 << 32) + (uint64_t)t.M - 1) / (uint64_t)t.M);
-    const AcXArgs<float> a = ac_x_args<float>(h, s, LineGeom{}, do_B, acoef, amp);
-    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X);
     return cuda_check(h, launch_xp<K>(a, t, mm, h->dflag, h->wait_polls, h->num_sms, h->stream), "acoustic x kernel");
   }
-  return ac_x<float, K>(h, s, do_B, acoef, amp);
+  if (xt_smem(t) > (size_t)h->smem_optin) {
+    h->err = "x patch does not fit in shared memory";
+    return LOSS_E_UNSUPPORTED;
+  }
+  return cuda_check(h, launch_xt<K>(a, t, h->stream), "acoustic x item kernels");
 }
 
 bool conv_z_used(const loss_ctx* h) {
@@ -547,6 +551,8 @@ static loss_status_t elastic3d_unstagger(loss_ctx* h, Shot& s) {
 // have the same arguments every step: k steps are captured once in a CUDA graph and replayed.  Arithmetic is that
 // of the per-shot schedule, so both give the same fields and traces.
 
+static bool conv_batch_ok(const loss_ctx* h);
+
 bool batch_eligible(const loss_ctx* h) {
   if (h->shots.empty()) return false;
   if (!(h->graph_steps > 0 || (h->batched && h->shots.size() > 1))) return false;
@@ -555,6 +561,11 @@ bool batch_eligible(const loss_ctx* h) {
     if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2 || s.esize != s0.esize || s.kahan != s0.kahan ||
         any_nonuniform(s))
       return false;
+  // without the batched convolution kernels the batch runs the line kernels, which hold whole rows: shots with
+  // rows the whole-row kernels do not take stay on the per-shot schedule (the (row, patch) item kernels)
+  if (s0.esize == 4 && !conv_batch_ok(h))
+    for (const Shot& s : h->shots)
+      if (s.n[2] > 2048) return false;
   return true;
 }
 

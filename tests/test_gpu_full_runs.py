@@ -152,6 +152,13 @@ def test_layered_2049_full_run_line_kernels(pkg):
     assert max(errs.values()) < TOL["fp32_kahan"], errs
 
 
+def test_layered_2049_full_run_item_kernels(pkg):
+    """The same run with the x part on (row, patch) items, the form rows too long for the pipelined x kernel take
+    (FP32 + compensation)."""
+    errs = _single(pkg, "acoustic2d_layered", "fp32_kahan", ACOUSTIC, family="convolution_items")
+    assert max(errs.values()) < TOL["fp32_kahan"], errs
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
 def test_elastic_257_full_run(pkg, prec):
     """257^3 points, 4 x 4 x 4 patches, homogeneous, explosive + shear source, 1000 steps; v1, v2, v3 on the top
