@@ -47,7 +47,7 @@ __device__ __forceinline__ float xt_junction(const float* __restrict__ S, const 
 }
 
 template <bool B, bool KAHAN>
-__global__ void __launch_bounds__(32 * kXtWarps) k_xt(AcXArgs<float> a, TileGeom t, int nitems) {
+__global__ void __launch_bounds__(32 * kXtWarps, 4) k_xt(AcXArgs<float> a, TileGeom t, int nitems) {
   extern __shared__ __align__(16) float xsm[];
   __shared__ float rpow[kFirPow];
   fill_rpow(rpow, t.r);
