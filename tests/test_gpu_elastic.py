@@ -105,6 +105,16 @@ def test_anisotropic_grid_three_forces_tiles(pkg, prec):
     assert max(errs.values()) < TOL[prec], errs
 
 
+@pytest.mark.parametrize("prec,family", [("fp64", None), ("fp32_kahan", "convolution"), ("fp32_kahan", "line")])
+def test_one_patch_per_axis(pkg, prec, family):
+    """25^3 points in one patch per axis (only the one-sided end closures, no interior junction), explosive +
+    shear source, 5-point layer, 40 steps."""
+    w = elastic3d_homogeneous(n=24, p=1, n_nb=8, steps=40, pml_width=5, precision=prec)
+    w = dataclasses.replace(w, f0=40.0, t0=1.2 / 40.0)
+    errs = _compare(pkg, w, prec, w.steps, family=family)
+    assert max(errs.values()) < TOL[prec], errs
+
+
 def test_full_size_homogeneous_one_step(pkg):
     """257^3 points in 4 x 4 x 4 patches (the homogeneous 3-D benchmark geometry), FP32 + Kahan, after the
     staggered start and one step, every field element-wise against the oracle."""
