@@ -14,6 +14,7 @@ about 2^4 when h is halved (the time step, at 0.1 h / c, plays no visible part).
 source time, kappa or b would leave a difference that does not converge.
 """
 import dataclasses
+import functools
 import math
 
 import numpy as np
@@ -29,8 +30,13 @@ def _ricker_rate(t, f0, t0):
     return -dadt * np.exp(-a) * (3.0 - 2.0 * a)
 
 
+@functools.lru_cache(maxsize=4)
+def _gauss_legendre(nodes):
+    return np.polynomial.legendre.leggauss(nodes)
+
+
 def _exact_sigma(points, t, c, f0, t0, amp, nodes=300):
-    k, wq = np.polynomial.legendre.leggauss(nodes)
+    k, wq = _gauss_legendre(nodes)
     out = 0.0
     for r, weight in points:
         if c * t <= r:
