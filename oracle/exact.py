@@ -25,6 +25,8 @@ The k-integral is a Gauss-Legendre sum on [0, kmax]; A(k) is below 1e-34 at k = 
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 from scipy.special import j0, j1
 
@@ -49,10 +51,16 @@ def _time_law(k, steps, dt, discrete, c):
     return np.cos(c * k * t), np.sin(c * k * t)
 
 
+@functools.lru_cache(maxsize=8)
+def _gauss_legendre(nodes: int):
+    """Gauss-Legendre nodes and weights on [-1, 1] (computed once per node count; callers do not modify them)."""
+    return np.polynomial.legendre.leggauss(nodes)
+
+
 def pulse_radial(r, steps: int, dt: float, discrete: bool = True, a: float = PULSE_A, c: float = PULSE_C,
                  rho: float = PULSE_RHO, nodes: int = 600, kmax: float = 40.0):
     """(sigma, v_r) at radii r after ``steps`` steps of length dt (time t = steps * dt)."""
-    k, wq = np.polynomial.legendre.leggauss(nodes)
+    k, wq = _gauss_legendre(nodes)
     k = 0.5 * kmax * (k + 1.0)
     wq = 0.5 * kmax * wq
     S, U = _time_law(k, steps, dt, discrete, c)
