@@ -12,9 +12,8 @@ for one workload run over its whole length:
 * ``norm_<field>``: the full-field L2 norm of every field at the checkpoints.
 
 The receivers sit where the wavefield is: lines through the source (2-D; for the survey shots the receiver row and
-the source column) or lines on the receiver plane (3-D: z = 0 for the homogeneous run, the top of the physical
-domain for the heterogeneous one), 33 points each; the workloads' own receiver sets are whole planes or rows and too
-large to store for every step.
+the source column) or lines on the receiver plane (3-D: the top of the physical domain, z = pml_width), 33 points
+each; the workloads' own receiver sets are whole planes or rows and too large to store for every step.
 
 Usage: python tests/golden/make_full_runs.py [name ...]     (default: every name of golden_names(); the 3-D runs
 take hours of CPU time on 8 cores)
@@ -83,7 +82,7 @@ def golden_workload(name: str):
         return dataclasses.replace(w, receivers={"sigma": _rcv_2d_through_source(w)}), 16
     if name == "elastic3d_homogeneous":
         w = W.elastic3d_homogeneous(precision="fp64")
-        r = _rcv_plane_lines(w)
+        r = _rcv_plane_lines(w, w.pml_width)
         return dataclasses.replace(w, receivers={"v1": r, "v2": r, "v3": r}), 16
     if name == "elastic3d_heterogeneous":
         w = W.elastic3d_heterogeneous(precision="fp64")
