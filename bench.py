@@ -110,8 +110,7 @@ def _dist():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region (every 50 ms: the timed
-    steps of the 2-D workload take tens of milliseconds)."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
     def __init__(self, index):
         self.index = index
@@ -126,7 +125,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
