@@ -425,7 +425,10 @@ def run_ours(args):
     clk = Clocks(local)
     clk.start()
     time.sleep(0.5)
-    g.step(args.warmup)
+    # warm-up steps, each after a flush as in the timed region (the flush's kernels load on first use)
+    for _ in range(args.warmup):
+        flush()
+        g.step(1)
     g.sync()
     g.profile(False)  # counts launches, records no per-launch events
     barrier()
