@@ -771,9 +771,10 @@ __device__ __forceinline__ void xp_init_barriers(uint64_t* bar) {
 // bulk-copies (TMA) the next row's arrays into the other of two shared-memory stages while the block computes the
 // current row, so HBM streams while the block computes.  Waits on the stage barriers are bounded: on a timeout
 // the block records it in *err, waits (bounded) for its copy in flight and stops.
-template <bool KAHAN>
-__global__ void __launch_bounds__(256, 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic, int* err,
-                                                unsigned polls) {
+// WIDE: rows of 2050 to 4097 points, one chunk per thread in blocks of up to 512 threads, one block per SM.
+template <bool KAHAN, bool WIDE>
+__global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2) k_xp(AcXArgs<float> a, TileGeom t, unsigned mmagic,
+                                                                       int* err, unsigned polls) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ float rpow[kFirPow];
   __shared__ float dlf[65];
@@ -1087,8 +1088,12 @@ cudaError_t launch_xp(const AcXArgs<float>& a, const TileGeom& t, unsigned mmagi
   unsigned pl = polls;
   void* argv[] = {&aa, &tt, &mm, &e, &pl};
   const int threads = (((t.n + 7) / 8 + 31) / 32) * 32;
+  if (threads > 256) {
+    const int grid = t.ncross < num_sms ? t.ncross : num_sms;
+    return tile_launch(k_xp<KAHAN, true>, grid, threads, xp_smem(t, KAHAN), st, argv);
+  }
   const int grid = t.ncross < 2 * num_sms ? t.ncross : 2 * num_sms;
-  return tile_launch(k_xp<KAHAN>, grid, threads, xp_smem(t, KAHAN), st, argv);
+  return tile_launch(k_xp<KAHAN, false>, grid, threads, xp_smem(t, KAHAN), st, argv);
 }
 template cudaError_t launch_xp<false>(const AcXArgs<float>&, const TileGeom&, unsigned, int*, unsigned, int,
                                       cudaStream_t);

@@ -202,10 +202,10 @@ static loss_status_t ensure_delta_weights(loss_ctx* h, Shot& s, int k) {
   return LOSS_OK;
 }
 
-// The pipelined x kernel takes rows of at most 2048 points in at most 64 patches whose length is a multiple of 8,
-// with the staged rows within shared memory.
+// The pipelined x kernel takes rows of at most 4097 points (blocks of 256 threads up to 2049, of 512 above) in at
+// most 64 patches whose length is a multiple of 8, with the staged rows within shared memory.
 static bool xp_ok(const loss_ctx* h, const Shot& s, const TileGeom& t) {
-  return h->tiled != LOSS_KERNELS_CONVOLUTION_ITEMS && s.n[2] <= 2048 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 &&
+  return h->tiled != LOSS_KERNELS_CONVOLUTION_ITEMS && s.n[2] <= 4096 && s.p[2] <= 64 && (s.n[2] / s.p[2]) % 8 == 0 &&
          xp_smem(t, s.kahan) + 2048 <= (size_t)h->smem_optin;
 }
 
@@ -776,7 +776,7 @@ static bool conv_batch_ok(const loss_ctx* h) {
     }
     int thr;
     TileGeom t = tile_geom(s, 2, &thr);
-    if (!xp_ok(h, s, t)) return false;
+    if (s.n[2] > 2048 || !xp_ok(h, s, t)) return false;  // the batched x kernel takes blocks of at most 256 threads
     ts.push_back(t);
     threads = std::max(threads, thr);
   }
