@@ -20,10 +20,15 @@ of Sec. 3.1 and 3.2 with the uniform B-spline values replaced by those of cubic 
 
 With n_nb >= N every sum is complete and the result is the natural cubic spline through the samples (pinned
 against scipy's CubicSpline in the tests); on a uniform grid it equals ``spline.derivative_1d``.
+
+6. ``layer_profiles``: the absorbing layer of Sec. 3.3 on such an axis, its profiles taken on the physical distance
+   into the layer (the paper defines them on a uniform grid, where distance and point count agree); used by
+   ``simulation`` for the 2-D acoustic step with layers.
 """
 from __future__ import annotations
 
 import functools
+import math
 
 import numpy as np
 from scipy.interpolate import BSpline
@@ -203,14 +208,39 @@ class Operator:
         return self.D(f, component_axis(comp, self.dim))
 
 
+def layer_profiles(x: np.ndarray, width: int, R: float, k_max: float, f0: float, c_max: float):
+    """The absorbing-layer profiles (d, k, alpha) of ``wave.PML`` along an axis with knots x, taken on the physical
+    distance into each layer: the layer is the outer ``width`` intervals at each end, of thickness L = x_W - x_0
+    (low end) or x_N - x_{N-W} (high end); a knot at distance s inside it has the normalised depth r = s / L, and
+    d = d0 r^2 with d0 = -3 c_max log(R) / (2 L), k = 1 + (k_max - 1) r, alpha = pi f0 (1 - r).  On equally
+    spaced knots these are the profiles of ``wave.PML``."""
+    x = np.asarray(x, dtype=np.float64)
+    N = len(x) - 1
+    d = np.zeros(N + 1)
+    r = np.zeros(N + 1)
+    for lo, hi, inner in ((0, width, x[width]), (N - width, N, x[N - width])):
+        L = abs(inner - (x[0] if lo == 0 else x[N]))
+        d0 = -3.0 * c_max * math.log(R) / (2.0 * L)
+        idx = np.arange(lo, hi + 1)
+        rr = np.abs(x[idx] - inner) / L
+        r[idx] = np.maximum(r[idx], rr)
+        d[idx] = np.maximum(d[idx], d0 * rr**2)
+    return d, 1.0 + (k_max - 1.0) * r, math.pi * f0 * (1.0 - r)
+
+
 def simulation(w, knots, state=None):
     """A ``wave.Simulation`` of workload w whose derivatives use the given knots (dict axis -> coordinates).  The
-    time stepping is the literal Strang sequence of ``wave``; absorbing layers and point sources, whose profiles
-    are defined on the uniform spacing, are not supported on such grids."""
+    time stepping is the literal Strang sequence of ``wave``; an absorbing layer takes its profiles on the
+    physical distance into the layer (``layer_profiles``).  Point sources, whose profile is defined on the uniform
+    spacing, are not supported on such grids."""
     from .wave import Simulation
 
-    if getattr(w, "pml_width", 0) or w.src_kinds:
-        raise ValueError("non-uniform grids: no absorbing layer and no point source")
+    if w.src_kinds:
+        raise ValueError("non-uniform grids: no point source")
     sim = Simulation(w, state=state)
     sim.op = Operator(w.n, w.p, w.h, w.n_nb, knots)
+    if sim.pml is not None:
+        vp = w.model()[0]
+        for a, x in knots.items():
+            sim.pml.prof[int(a)] = layer_profiles(x, w.pml_width, w.pml_R, w.pml_kmax, w.f0, float(np.max(vp)))
     return sim

@@ -136,3 +136,65 @@ def test_uniform_knots_step_like_the_uniform_oracle():
     b = nu.simulation(w, {0: x, 1: x}, state=st).step(20, record=False)
     for f in ("sigma", "v1", "v3"):
         assert np.abs(a.state[f] - b.state[f]).max() < 1e-12 * np.abs(a.state[f]).max()
+
+
+def test_layer_profiles_on_equal_knots_are_the_uniform_layers():
+    """On equally spaced knots the physical-distance profiles are wave.PML's, value for value."""
+    from oracle.wave import PML
+
+    for n, W, h in ((64, 12, 10.0), (40, 8, 0.25)):
+        x = h * np.arange(n + 1)
+        ref = PML((n,), (h,), W, 1e-6, 1.0, 15.0, 2000.0).prof[0]
+        got = nu.layer_profiles(x, W, 1e-6, 1.0, 15.0, 2000.0)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+
+def _padded_stretched(nt, h, pad, eps=0.3):
+    xi = -5.0 + h * (np.arange(nt + 1) - pad)
+    half = xi[-1]
+    return xi + eps * (half / np.pi) * np.sin(np.pi * xi / half)
+
+
+def test_uniform_knots_with_a_layer_step_like_the_uniform_oracle():
+    import dataclasses
+
+    from oracle.wave import Simulation
+    from synth import gaussian_pulse_2d
+
+    w, s0 = gaussian_pulse_2d(32, p=2, n_nb=12, dt=1e-4, steps=60, pad=8)
+    w = dataclasses.replace(w, pml_width=8)
+    st = {"sigma": s0, "v1": np.zeros(w.shape), "v3": np.zeros(w.shape)}
+    a = Simulation(w, state=st).step(60, record=False)
+    x = w.h[0] * np.arange(w.n[0] + 1)
+    b = nu.simulation(w, {0: x, 1: x}, state=st).step(60, record=False)
+    for f in ("sigma", "v1", "v3"):
+        assert np.abs(a.state[f] - b.state[f]).max() < 1e-10 * np.abs(a.state[f]).max()
+
+
+def test_layer_absorbs_on_stretched_knots():
+    """The Gaussian pulse on knots stretched by a factor 1.86, with 8-interval layers outside [-5, 5]^2 (2.5 m
+    thick): after 0.36 s the pressure energy left on the grid is below 1 % of the initial one and within a factor
+    3 of the uniform grid's with the same layers (measured 2.6e-3 and 4.7e-3), while without layers the
+    natural-spline end modes make it grow past the initial energy."""
+    import dataclasses
+
+    from oracle.wave import Simulation
+    from synth import gaussian_pulse_2d
+
+    n, pad, steps = 32, 8, 3600
+    w, s0u = gaussian_pulse_2d(n, p=2, n_nb=12, dt=1e-4, steps=steps, pad=pad)
+    x = _padded_stretched(n + 2 * pad, 10.0 / n, pad)
+    s0 = np.exp(-5.0 * (x[:, None] ** 2 + x[None, :] ** 2))
+    zero = np.zeros(w.shape)
+
+    def left(sim, init):
+        sim.step(steps, record=False)
+        return np.sum(sim.state["sigma"] ** 2) / np.sum(init**2)
+
+    wl = dataclasses.replace(w, pml_width=pad)
+    e_nu = left(nu.simulation(wl, {0: x, 1: x}, state={"sigma": s0, "v1": zero, "v3": zero}), s0)
+    e_u = left(Simulation(wl, state={"sigma": s0u, "v1": zero, "v3": zero}), s0u)
+    e_none = left(nu.simulation(w, {0: x, 1: x}, state={"sigma": s0, "v1": zero, "v3": zero}), s0)
+    assert e_nu < 1e-2 and e_nu < 3.0 * e_u, (e_nu, e_u)
+    assert e_none > 1.0, e_none
