@@ -914,15 +914,45 @@ loss_status_t loss_set_source(loss_handle_t h, int32_t shot, const int64_t idx[3
   return LOSS_OK;
 }
 
-static void pml_table(const Shot& s, int k, double tau, std::vector<double>& tab) {
+// Layer profile of axis slot k at position i: damping d and normalised depth r (paper Sec. 3.3, d = d0 r^2).  On
+// an axis with knots of its own the depth is the physical distance into the layer over the layer's thickness,
+// each end with its own thickness and d0; equally spaced knots give the same values as the point count.
+static void pml_profile(const Shot& s, int k, std::vector<double>& d, std::vector<double>& r) {
   const int n = (int)s.n[k];
   const int W = s.pml_width;
+  d.assign(n + 1, 0.0);
+  r.assign(n + 1, 0.0);
+  if (s.coords[k].empty()) {
+    const double L = W * s.h[k];
+    const double d0 = -3.0 * s.vmax * std::log(s.pml_R) / (2.0 * L);
+    for (int i = 0; i <= n; ++i) {
+      r[i] = std::max(std::max((double)(W - i), (double)(i - (n - W))), 0.0) / W;
+      d[i] = d0 * r[i] * r[i];
+    }
+    return;
+  }
+  const std::vector<double>& x = s.coords[k];
+  for (int side = 0; side < 2; ++side) {
+    const int lo = side == 0 ? 0 : n - W, hi = side == 0 ? W : n;
+    const double inner = side == 0 ? x[W] : x[n - W];
+    const double L = std::fabs(inner - (side == 0 ? x[0] : x[n]));
+    const double d0 = -3.0 * s.vmax * std::log(s.pml_R) / (2.0 * L);
+    for (int i = lo; i <= hi; ++i) {
+      const double rr = std::fabs(x[i] - inner) / L;
+      r[i] = std::max(r[i], rr);
+      d[i] = std::max(d[i], d0 * rr * rr);
+    }
+  }
+}
+
+static void pml_table(const Shot& s, int k, double tau, std::vector<double>& tab) {
+  const int n = (int)s.n[k];
   tab.assign((size_t)4 * (n + 1), 0.0);
-  const double L = W * s.h[k];
-  const double d0 = -3.0 * s.vmax * std::log(s.pml_R) / (2.0 * L);
+  std::vector<double> dd, rr;
+  pml_profile(s, k, dd, rr);
   for (int i = 0; i <= n; ++i) {
-    const double r = std::max(std::max((double)(W - i), (double)(i - (n - W))), 0.0) / W;
-    const double d = d0 * r * r, kk = 1.0 + (s.pml_kmax - 1.0) * r, al = M_PI * s.pml_f0 * (1.0 - r);
+    const double r = rr[i];
+    const double d = dd[i], kk = 1.0 + (s.pml_kmax - 1.0) * r, al = M_PI * s.pml_f0 * (1.0 - r);
     double E = 1.0, cp = 0.0, c1 = 0.0, c2 = tau;
     if (d > 0.0) {
       const double beta = d / kk + al;
@@ -978,23 +1008,10 @@ loss_status_t loss_set_pml(loss_handle_t h, int32_t shot, int32_t width, double 
   s->pml_kmax = k_max;
   s->pml_f0 = f0;
   if (!s->pml_on) return LOSS_OK;
+  LOSS_TRY(pml_upload_tables(h, *s));
   const size_t fb = (size_t)s->total * s->esize;
-  const double taus[3] = {s->d.dt, 0.5 * s->d.dt, -0.5 * s->d.dt};
   for (int k = 0; k < 3; ++k) {
     if (s->dim == 2 && k == 1) continue;
-    for (int v = 0; v < 3; ++v) {
-      std::vector<double> tab;
-      pml_table(*s, k, taus[v], tab);
-      if (!s->pml_tab[k][v]) LOSS_TRY(dev_alloc(h, tab.size() * s->esize, &s->pml_tab[k][v]));
-      if (s->esize == 8) {
-        LOSS_TRY(cuda_check(h, cudaMemcpy(s->pml_tab[k][v], tab.data(), tab.size() * 8, cudaMemcpyHostToDevice),
-                            "copy pml"));
-      } else {
-        std::vector<float> f(tab.begin(), tab.end());
-        LOSS_TRY(cuda_check(h, cudaMemcpy(s->pml_tab[k][v], f.data(), f.size() * 4, cudaMemcpyHostToDevice),
-                            "copy pml"));
-      }
-    }
     if (s->d.physics == LOSS_ELASTIC) continue;
     if (!s->psi[k]) LOSS_TRY(dev_zero_alloc(h, fb, &s->psi[k]));
     if (!s->phi[k]) LOSS_TRY(dev_zero_alloc(h, fb, &s->phi[k]));
@@ -1252,6 +1269,29 @@ loss_status_t loss_set_state(loss_handle_t h, const void* blob, size_t bytes) {
 // ----------------------------------------------------------------------------------------------------------------
 // Internal pieces used above.
 namespace lossk {
+
+// The layer coefficient tables of every axis slot for the sub-step lengths dt, dt/2 and -dt/2.
+loss_status_t pml_upload_tables(loss_ctx* h, Shot& s) {
+  const double taus[3] = {s.d.dt, 0.5 * s.d.dt, -0.5 * s.d.dt};
+  for (int k = 0; k < 3; ++k) {
+    if (s.dim == 2 && k == 1) continue;
+    for (int v = 0; v < 3; ++v) {
+      std::vector<double> tab;
+      pml_table(s, k, taus[v], tab);
+      if (!s.pml_tab[k][v]) LOSS_TRY(dev_alloc(h, tab.size() * s.esize, &s.pml_tab[k][v]));
+      if (s.esize == 8) {
+        LOSS_TRY(cuda_check(h, cudaMemcpy(s.pml_tab[k][v], tab.data(), tab.size() * 8, cudaMemcpyHostToDevice),
+                            "copy pml"));
+      } else {
+        std::vector<float> f(tab.begin(), tab.end());
+        LOSS_TRY(cuda_check(h, cudaMemcpy(s.pml_tab[k][v], f.data(), f.size() * 4, cudaMemcpyHostToDevice),
+                            "copy pml"));
+      }
+    }
+  }
+  return LOSS_OK;
+}
+
 
 bool is_velocity(int f) { return f == LOSS_FIELD_V1 || f == LOSS_FIELD_V2 || f == LOSS_FIELD_V3; }
 

@@ -44,6 +44,7 @@ struct Shot {
   double* W[3] = {};     // PMBC weights per axis slot, scaled by h/3
   double* Wd[3] = {};     // junction-correction weights of the FP32 truncated-convolution kernels (on first use)
   void* nu_tab[3] = {};   // non-uniform axis slot (loss_set_coordinates): PMBC weights and elimination tables
+  std::vector<double> coords[3];  // the knots loss_set_coordinates gave an axis slot (empty: equally spaced)
   bool has_model = false;
   double vmax = 0.0;
   bool b_const = false;  // density constant: buoyancy passed as a scalar, the b array is not read
@@ -252,6 +253,8 @@ cudaError_t launch_ac_z_batch(const AcZArgs<T>* tab, const int* tile0, int nshot
 template <typename T>
 cudaError_t launch_gather_batch(const GatherJob<T>* jobs, int njobs, int64_t max_cnt, cudaStream_t st);
 cudaError_t launch_tick(StepClock* c, int n, cudaStream_t st);
+// loss_api.cu: the absorbing-layer tables of every axis (after loss_set_pml or a change of knots)
+loss_status_t pml_upload_tables(loss_ctx* h, Shot& s);
 // loss_copy.cu: dst[r * pitch + c] = src[r * cols + c] on the device
 cudaError_t launch_pitch_in(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,
                             int num_sms, cudaStream_t st);

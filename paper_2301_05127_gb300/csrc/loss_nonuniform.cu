@@ -285,6 +285,57 @@ __global__ void __launch_bounds__(256) k_nu_update(T* __restrict__ u, T* __restr
   }
 }
 
+// With absorbing layers.  Velocity v along axis slot k: v += b X, X the exact sub-flow of the layer over tau
+// (PmlAxis::step, which also advances the memory variable) at positions inside the layer, -tau g elsewhere.
+template <typename T, bool K>
+__global__ void __launch_bounds__(256) k_nu_vel_pml(T* __restrict__ u, T* __restrict__ c, const T* __restrict__ g,
+                                                    const T* __restrict__ b, T b0, T tau, PmlAxis<T> pa, T* mem,
+                                                    int64_t px, int nx, int along_x, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t row = i / px;
+    const int col = (int)(i - row * px);
+    if (col > nx) continue;  // row padding
+    const int pos = along_x ? col : (int)row;
+    const T gv = g[i];
+    const T X = pa.in(pos) ? pa.step(mem, i, pos, gv) : -tau * gv;
+    const T delta = (b ? b[i] : b0) * X;
+    if constexpr (K) {
+      float v = u[i], cc = c[i];
+      kahan_add(v, cc, delta);
+      u[i] = v;
+      c[i] = cc;
+    } else {
+      u[i] += delta;
+    }
+  }
+}
+// sigma += kappa (X_x + X_z) over tau, with the memory variables of both axes.
+template <typename T, bool K>
+__global__ void __launch_bounds__(256) k_nu_sig_pml(T* __restrict__ u, T* __restrict__ c, const T* __restrict__ gx,
+                                                    const T* __restrict__ gz, const T* __restrict__ kappa, T tau,
+                                                    PmlAxis<T> pxa, T* memx, PmlAxis<T> pza, T* memz, int64_t px,
+                                                    int nx, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t row = i / px;
+    const int col = (int)(i - row * px);
+    if (col > nx) continue;
+    const T ax = gx[i], az = gz[i];
+    const T Xx = pxa.in(col) ? pxa.step(memx, i, col, ax) : -tau * ax;
+    const T Xz = pza.in((int)row) ? pza.step(memz, i, (int)row, az) : -tau * az;
+    const T delta = kappa[i] * (Xx + Xz);
+    if constexpr (K) {
+      float v = u[i], cc = c[i];
+      kahan_add(v, cc, delta);
+      u[i] = v;
+      c[i] = cc;
+    } else {
+      u[i] += delta;
+    }
+  }
+}
+
 loss_status_t nu_ensure_axes(loss_ctx* h, Shot& s) {
   for (int k = 0; k < 3; ++k) {
     if (s.dim == 2 && k == 1) continue;
@@ -311,32 +362,59 @@ static loss_status_t nu_update(loss_ctx* h, Shot& s, int field, const void* g0, 
   return cuda_check(h, cudaGetLastError(), "non-uniform update kernel");
 }
 
+// Layer coefficients of axis slot k for the sub-step length tau (tables for dt and dt / 2).
+template <typename T>
+static PmlAxis<T> nu_pml_axis(const Shot& s, int k, double tau) {
+  return PmlAxis<T>{(const T*)s.pml_tab[k][tau == s.d.dt ? 0 : 1], s.pml_width, (int)s.n[k], nullptr};
+}
+
 template <typename T, bool K>
 static loss_status_t nu_step_t(loss_ctx* h, Shot& s) {
   const double dt = s.d.dt;
   T* t0 = (T*)s.tmp[0];
   T* t1 = (T*)s.tmp[1];
   const void* b = s.b_const ? nullptr : s.model[1];
+  const int grid = (int)std::min<int64_t>((s.total + 255) / 256, 8LL * h->num_sms);
+  const int nx = (int)s.n[2];
+  // velocity along slot k over dt / 2 with the layer's sub-flow (memory psi)
+  auto vel_pml = [&](int field, const T* g, int k) -> loss_status_t {
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X2);
+    k_nu_vel_pml<T, K><<<grid, 256, 0, h->stream>>>((T*)s.field[field], K ? (T*)s.comp[field] : nullptr, g,
+                                                     (const T*)b, (T)s.b0, (T)(0.5 * dt), nu_pml_axis<T>(s, k, 0.5 * dt),
+                                                     (T*)s.psi[k], s.px, nx, k == 2 ? 1 : 0, s.total);
+    return cuda_check(h, cudaGetLastError(), "non-uniform layer update kernel");
+  };
   auto half_A = [&]() -> loss_status_t {
     NU_TRY(nu_launch<T>(h, s, 2, (const T*)s.field[LOSS_FIELD_SIGMA], t0, nullptr, s.sy, s.sz,
                         LOSS_KERNEL_ACOUSTIC_X));
     NU_TRY(nu_launch<T>(h, s, 0, (const T*)s.field[LOSS_FIELD_SIGMA], t1, nullptr, s.sy, s.sz,
                         LOSS_KERNEL_ACOUSTIC_Z));
+    if (s.pml_on) {
+      NU_TRY(vel_pml(LOSS_FIELD_V1, t0, 2));
+      return vel_pml(LOSS_FIELD_V3, t1, 0);
+    }
     NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_V1, t0, nullptr, b, s.b0, -0.5 * dt)));
     return nu_update<T, K>(h, s, LOSS_FIELD_V3, t1, nullptr, b, s.b0, -0.5 * dt);
   };
   NU_TRY(half_A());
   NU_TRY(nu_launch<T>(h, s, 2, (const T*)s.field[LOSS_FIELD_V1], t0, nullptr, s.sy, s.sz, LOSS_KERNEL_ACOUSTIC_X));
   NU_TRY(nu_launch<T>(h, s, 0, (const T*)s.field[LOSS_FIELD_V3], t1, nullptr, s.sy, s.sz, LOSS_KERNEL_ACOUSTIC_Z));
-  NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_SIGMA, t0, t1, s.model[0], 0.0, -dt)));
+  if (s.pml_on) {
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X2);
+    k_nu_sig_pml<T, K><<<grid, 256, 0, h->stream>>>(
+        (T*)s.field[LOSS_FIELD_SIGMA], K ? (T*)s.comp[LOSS_FIELD_SIGMA] : nullptr, t0, t1, (const T*)s.model[0],
+        (T)dt, nu_pml_axis<T>(s, 2, dt), (T*)s.phi[2], nu_pml_axis<T>(s, 0, dt), (T*)s.phi[0], s.px, nx, s.total);
+    NU_TRY(cuda_check(h, cudaGetLastError(), "non-uniform layer update kernel"));
+  } else {
+    NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_SIGMA, t0, t1, s.model[0], 0.0, -dt)));
+  }
   return half_A();
 }
 
 loss_status_t nu_step(loss_ctx* h, Shot& s) {
   if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2)
     return fail_msg(h, LOSS_E_UNSUPPORTED, "time steps on non-uniform grids are built for 2-D acoustic grids");
-  if (s.pml_on || s.src_on)
-    return fail_msg(h, LOSS_E_UNSUPPORTED, "non-uniform grids: no absorbing layer and no point source");
+  if (s.src_on) return fail_msg(h, LOSS_E_UNSUPPORTED, "non-uniform grids: no point source");
   NU_TRY(nu_ensure_axes(h, s));
   if (s.esize == 8) return nu_step_t<double, false>(h, s);
   if (s.kahan) return nu_step_t<float, true>(h, s);
@@ -350,10 +428,14 @@ loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x) {
   if (!x) {
     if (s.nu_tab[k]) dev_free(h, s.nu_tab[k]);
     s.nu_tab[k] = nullptr;
-    return LOSS_OK;
+    s.coords[k].clear();
+  } else {
+    std::vector<double> xs(x, x + s.n[k] + 1);
+    NU_TRY(nu_upload(h, s, k, xs));
+    s.coords[k] = xs;
   }
-  std::vector<double> xs(x, x + s.n[k] + 1);
-  return nu_upload(h, s, k, xs);
+  // the absorbing layer's profiles follow the knots
+  return s.pml_on ? pml_upload_tables(h, s) : LOSS_OK;
 }
 
 }  // namespace lossk
