@@ -420,10 +420,24 @@ static loss_status_t copy_in(loss_ctx* h, const Shot& s, void* dst, const void* 
                     "copy in");
 }
 
-// Host upload of a field: a pinned host array goes through one 1-D copy into a dense device staging buffer and
-// the pitch kernel (faster than a 2-D copy from host memory); pageable arrays take the 2-D copy.
+// Device address of a pinned host array that kernels may read and write directly, or null (pageable memory).
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Host upload of a field: the pitch kernel reads a mapped pinned host array directly and spreads it into the
+// padded rows; pageable arrays take the 2-D copy.
 static loss_status_t upload_field(loss_ctx* h, const Shot& s, void* dst, const void* src, int mem) {
   if (mem != LOSS_MEM_HOST) return copy_in(h, s, dst, src, mem);
+  const void* msrc = mapped_host(src);
+  if (msrc)
+    return cuda_check(h, launch_pitch_in(msrc, dst, s.len[0] * s.len[1], s.len[2], s.px, s.esize, h->num_sms,
+                                         h->stream), "pitch kernel");
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
     cudaGetLastError();
@@ -444,6 +458,12 @@ static loss_status_t upload_field(loss_ctx* h, const Shot& s, void* dst, const v
 }
 
 static loss_status_t copy_out(loss_ctx* h, const Shot& s, void* dst, const void* src, int mem) {
+  if (mem == LOSS_MEM_HOST) {
+    void* mdst = mapped_host(dst);
+    if (mdst)
+      return cuda_check(h, launch_pitch_out(src, mdst, s.len[0] * s.len[1], s.len[2], s.px, s.esize, h->num_sms,
+                                            h->stream), "pitch kernel");
+  }
   const size_t w = (size_t)s.len[2] * s.esize;
   return cuda_check(h, cudaMemcpy2DAsync(dst, w, src, (size_t)s.px * s.esize, w, (size_t)(s.len[0] * s.len[1]),
                                          mem == LOSS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,

@@ -1,9 +1,11 @@
-// Dense -> pitched copy on the device, the second half of a host upload.
+// Dense <-> pitched copies on the device, the device half of host uploads and downloads.
 //
 // Fields live in HBM with rows padded to a multiple of 32 elements.  Copying a dense host array straight into that
 // layout takes a 2-D copy, which moves pinned host memory at about 130 GB/s on this machine against about 200 GB/s
-// for a 1-D copy of the same bytes; so a pinned host array is first copied 1-D into a dense device staging buffer
-// and then spread into the padded rows here, at HBM speed.
+// for a 1-D copy of the same bytes.  A pinned host array is mapped into the device's address space, so the pitch
+// kernels read (upload) or write (download) it directly and spread or gather the padded rows in the same pass;
+// end to end through the C ABI that measured 2.95 against 3.05 ms for a 20-step 2049^2 run with a staging buffer
+// and a 1-D copy.
 #include <cuda_runtime.h>
 
 #include "loss_host.h"
@@ -19,6 +21,30 @@ __global__ void __launch_bounds__(256) k_pitch_in(const T* __restrict__ src, T* 
     const int64_t r = i / cols;
     dst[r * pitch + (i - r * cols)] = src[i];
   }
+}
+
+// Pitched -> dense, the device half of a download into a mapped pinned host array (the stores cross the host link).
+template <typename T>
+__global__ void __launch_bounds__(256) k_pitch_out(const T* __restrict__ src, T* __restrict__ dst, int64_t rows,
+                                                   int64_t cols, int64_t pitch) {
+  const int64_t n = rows * cols;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t r = i / cols;
+    dst[i] = src[r * pitch + (i - r * cols)];
+  }
+}
+
+cudaError_t launch_pitch_out(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,
+                             int num_sms, cudaStream_t st) {
+  const int64_t n = rows * cols;
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 8LL * num_sms);
+  if (esize == 8)
+    k_pitch_out<double><<<grid, 256, 0, st>>>((const double*)src, (double*)dst, rows, cols, pitch);
+  else
+    k_pitch_out<float><<<grid, 256, 0, st>>>((const float*)src, (float*)dst, rows, cols, pitch);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pitch_in(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,

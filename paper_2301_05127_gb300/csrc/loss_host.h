@@ -258,6 +258,8 @@ loss_status_t pml_upload_tables(loss_ctx* h, Shot& s);
 // loss_copy.cu: dst[r * pitch + c] = src[r * cols + c] on the device
 cudaError_t launch_pitch_in(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,
                             int num_sms, cudaStream_t st);
+cudaError_t launch_pitch_out(const void* src, void* dst, int64_t rows, int64_t cols, int64_t pitch, size_t esize,
+                            int num_sms, cudaStream_t st);
 // loss_watch.cu: sets *flag to code (if it is still 0) when one of the n values at f is not finite
 cudaError_t launch_finite(const void* f, int64_t n, size_t esize, int* flag, int code, int num_sms, cudaStream_t st);
 template <bool KAHAN>

@@ -197,3 +197,29 @@ def test_fp32_kernel_families_on_uneven_geometries(pkg, family, geom):
                             receivers={"sigma": top}, f0=60.0, t0=1.2 / 60.0, dt=0.4 * 10.0 / 2600.0)
     errs = _compare(pkg, w, "fp32_kahan", 60, every=20, family=family)
     assert max(errs.values()) < TOL["fp32_kahan"], errs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_pinned_host_buffers(pkg, prec):
+    """Fields set from and read into pinned host tensors (the pitch kernels read and write the mapped host memory
+    directly) equal the copies through pageable numpy arrays, on a grid whose 101-point rows are padded in HBM."""
+    import torch
+
+    w = acoustic2d_small(n=100, p=4, steps=10, n_nb=10, pml_width=10)
+    g = pkg.Grid.from_workloads([w], precision=prec)
+    dt = g.dtype
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(w.shape).astype(dt)
+    g.set_field(0, "sigma", torch.from_numpy(a.copy()).pin_memory())
+    assert np.array_equal(g.get_field(0, "sigma"), a)
+    out = torch.empty(w.shape, dtype=tdt).pin_memory()
+    g.get_field(0, "sigma", out=out)
+    assert np.array_equal(out.numpy(), a)
+    g.step(5)
+    for f in ("sigma", "v1", "v3"):
+        ref = g.get_field(0, f)
+        out = torch.full(w.shape, float("nan"), dtype=tdt).pin_memory()
+        g.get_field(0, f, out=out)
+        assert np.array_equal(out.numpy(), ref), f
+    g.close()
