@@ -122,6 +122,17 @@ def _check(st, handle=None):
         raise LossError(st, msg)
 
 
+def _expect_buffer(a, shape, itemsize, what):
+    """Refuse an array or tensor that does not hold exactly the grid's points in the expected element size: the
+    library reads and writes the full dense extent behind a plain pointer."""
+    n = int(np.prod(shape))
+    size = a.size if isinstance(a, np.ndarray) else a.numel()
+    esize = a.itemsize if isinstance(a, np.ndarray) else a.element_size()
+    if size != n or esize != itemsize:
+        raise ValueError(f"{what}: expected {n} elements of {itemsize} bytes (shape {tuple(shape)}), "
+                         f"got {size} of {esize}")
+
+
 def _ptr_and_mem(a):
     """(pointer, mem) of a numpy array or a torch tensor."""
     if isinstance(a, np.ndarray):
@@ -249,6 +260,9 @@ class Grid:
             import torch
             cvt = lambda a: None if a is None else a.detach().to(torch.float64).contiguous()  # noqa: E731
             vp, vs, rho = cvt(vp), cvt(vs), cvt(rho)
+            for name, a in (("vp", vp), ("vs", vs), ("rho", rho)):
+                if a is not None:
+                    _expect_buffer(a, self.shape(shot), 8, name)
             mem = LOSS_MEM_DEVICE if vp.is_cuda else LOSS_MEM_HOST
             _check(lib().loss_set_model(self.h, shot, vp.data_ptr(), None if vs is None else vs.data_ptr(),
                                         rho.data_ptr(), mem), self.h)
@@ -256,6 +270,9 @@ class Grid:
         vp = np.ascontiguousarray(vp, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         vsa = None if vs is None else np.ascontiguousarray(vs, dtype=np.float64)
+        for name, a in (("vp", vp), ("vs", vsa), ("rho", rho)):
+            if a is not None:
+                _expect_buffer(a, self.shape(shot), 8, name)
         _check(lib().loss_set_model(self.h, shot, vp.ctypes.data, None if vsa is None else vsa.ctypes.data,
                                     rho.ctypes.data, LOSS_MEM_HOST), self.h)
 
@@ -273,12 +290,14 @@ class Grid:
     def set_field(self, shot, field, arr):
         if isinstance(arr, np.ndarray):
             arr = np.ascontiguousarray(arr, dtype=self.dtype)
+        _expect_buffer(arr, self.shape(shot), np.dtype(self.dtype).itemsize, field)
         ptr, mem = _ptr_and_mem(arr)
         _check(lib().loss_set_field(self.h, shot, FIELDS[field], ptr, mem), self.h)
 
     def get_field(self, shot, field, out=None):
         if out is None:
             out = np.empty(self.shape(shot), dtype=self.dtype)
+        _expect_buffer(out, self.shape(shot), np.dtype(self.dtype).itemsize, field)
         ptr, mem = _ptr_and_mem(out)
         _check(lib().loss_get_field(self.h, shot, FIELDS[field], ptr, mem), self.h)
         return out

@@ -89,3 +89,19 @@ def test_binding_fails_loudly_without_library(pkg, monkeypatch, tmp_path):
     monkeypatch.setattr(pkg, "_lib", None)
     with pytest.raises(ImportError):
         pkg.lib()
+
+
+def test_binding_refuses_buffers_of_the_wrong_size(pkg):
+    """The library reads and writes a field's whole dense extent behind a plain pointer, so the binding refuses an
+    array or tensor with another element count or element size before it calls the library."""
+    import numpy as np
+    import torch
+
+    from paper_2301_05127_gb300 import _expect_buffer
+
+    _expect_buffer(np.zeros((3, 4), np.float32), (3, 4), 4, "sigma")
+    _expect_buffer(torch.zeros(12, dtype=torch.float64), (3, 4), 8, "sigma")
+    for a, esize in ((np.zeros((3, 3), np.float32), 4), (np.zeros((3, 4), np.float64), 4),
+                     (torch.zeros(12, dtype=torch.float32), 8), (torch.zeros(13, dtype=torch.float64), 8)):
+        with pytest.raises(ValueError):
+            _expect_buffer(a, (3, 4), esize, "sigma")
