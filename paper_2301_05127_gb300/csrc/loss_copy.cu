@@ -4,8 +4,8 @@
 // layout takes a 2-D copy, which moves pinned host memory at about 130 GB/s on this machine against about 200 GB/s
 // for a 1-D copy of the same bytes.  A pinned host array is mapped into the device's address space, so the pitch
 // kernels read (upload) or write (download) it directly and spread or gather the padded rows in the same pass;
-// end to end through the C ABI that measured 2.95 against 3.05 ms for a 20-step 2049^2 run with a staging buffer
-// and a 1-D copy.
+// end to end through the C ABI that measured 2.95-3.00 against 3.05 ms for a 20-step 2049^2 run with a staging
+// buffer and a 1-D copy.
 #include <cuda_runtime.h>
 
 #include "loss_host.h"
