@@ -24,6 +24,10 @@ against scipy's CubicSpline in the tests); on a uniform grid it equals ``spline.
 6. ``layer_profiles``: the absorbing layer of Sec. 3.3 on such an axis, its profiles taken on the physical distance
    into the layer (the paper defines them on a uniform grid, where distance and point count agree); used by
    ``simulation`` for the 2-D acoustic step with layers.
+7. ``KnotSource``: the Gaussian source amplitude of Sec. 4.2 on such a grid, taken on the physical distance from
+   the source knot with the width of the uniform grid (w = 2 h), on the same block of 25 knots per axis, and
+   normalised with the knots' cell volumes (products of dual cell widths) so that it injects the same total as on
+   the uniform grid.
 """
 from __future__ import annotations
 
@@ -228,17 +232,62 @@ def layer_profiles(x: np.ndarray, width: int, R: float, k_max: float, f0: float,
     return d, 1.0 + (k_max - 1.0) * r, math.pi * f0 * (1.0 - r)
 
 
+def cell_widths(c: np.ndarray) -> np.ndarray:
+    """Dual cell width of every knot: half the distance between its neighbours (one-sided at the two ends)."""
+    c = np.asarray(c, dtype=np.float64)
+    v = np.empty_like(c)
+    v[1:-1] = 0.5 * (c[2:] - c[:-2])
+    v[0] = 0.5 * (c[1] - c[0])
+    v[-1] = 0.5 * (c[-1] - c[-2])
+    return v
+
+
+class KnotSource:
+    """Point source on a grid whose axes may carry knots: A(x) ~ exp(-|x - x0|^2 / (2 w^2)) with w = 2 h_a on axis a
+    (h the nominal spacing) in physical distance from the source knot, on the knots within 12 of it per axis
+    (clipped to the grid), normalised so that sum_i A_i V_i = amp with V_i the product of the knots' dual cell widths.
+    On equally spaced knots away from the grid ends this is ``wave.Source``."""
+
+    def __init__(self, index, kinds, f0, t0, amp, h, shape, knots):
+        from .wave import SOURCE_RADIUS, SOURCE_WIDTH
+
+        self.index = tuple(int(i) for i in index)
+        self.kinds = tuple(kinds)
+        self.f0, self.t0, self.amp = f0, t0, amp
+        d = len(shape)
+        lo = [max(0, self.index[a] - SOURCE_RADIUS) for a in range(d)]
+        hi = [min(shape[a] - 1, self.index[a] + SOURCE_RADIUS) for a in range(d)]
+        self.block = tuple(slice(lo[a], hi[a] + 1) for a in range(d))
+        g, v = [], []
+        for a in range(d):
+            c = np.asarray(knots[a], dtype=np.float64) if a in knots else h[a] * np.arange(shape[a], dtype=np.float64)
+            w = SOURCE_WIDTH * h[a]
+            g.append(np.exp(-((c[lo[a]:hi[a] + 1] - c[self.index[a]]) ** 2) / (2.0 * w * w)))
+            v.append(cell_widths(c)[lo[a]:hi[a] + 1])
+        G = functools.reduce(np.multiply.outer, g)
+        V = functools.reduce(np.multiply.outer, v)
+        self.profile = amp * G / float(np.sum(G * V))
+
+    def add(self, field: np.ndarray, scale: float, t: float):
+        """field += scale * f_r(t) * A(x) on the profile block."""
+        from .wave import ricker
+
+        field[self.block] += scale * ricker(t, self.f0, self.t0) * self.profile
+
+
 def simulation(w, knots, state=None):
     """A ``wave.Simulation`` of workload w whose derivatives use the given knots (dict axis -> coordinates).  The
     time stepping is the literal Strang sequence of ``wave``; an absorbing layer takes its profiles on the
-    physical distance into the layer (``layer_profiles``).  Point sources, whose profile is defined on the uniform
-    spacing, are not supported on such grids."""
+    physical distance into the layer (``layer_profiles``) and a pressure source its amplitude on the physical
+    distance from the source knot (``KnotSource``).  Other source kinds are not supported on such grids."""
     from .wave import Simulation
 
-    if w.src_kinds:
-        raise ValueError("non-uniform grids: no point source")
+    if w.src_kinds and (w.dim != 2 or tuple(w.src_kinds) != ("pressure",)):
+        raise ValueError("non-uniform grids: only a pressure source in 2-D")
     sim = Simulation(w, state=state)
     sim.op = Operator(w.n, w.p, w.h, w.n_nb, knots)
+    if w.src_kinds:
+        sim.src = KnotSource(w.src_index, w.src_kinds, w.f0, w.t0, w.amp, w.h, w.shape, knots)
     if sim.pml is not None:
         vp = w.model()[0]
         for a, x in knots.items():
