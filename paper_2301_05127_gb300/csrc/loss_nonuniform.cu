@@ -336,6 +336,63 @@ __global__ void __launch_bounds__(256) k_nu_sig_pml(T* __restrict__ u, T* __rest
   }
 }
 
+// Pressure source on knots: sigma += amp gz[oz] gx[ox] over the 25 x 25 knots around the source knot (zs, xs); gz,
+// gx: the Gaussian of width 2 h on the physical distance from the source knot (0 off the grid); amp: dt f_r(t)
+// times the amplitude over the cell-volume weighted sum of the profile.
+struct NuSrc {
+  int zs, xs;
+  double amp;
+  double gz[25], gx[25];
+};
+template <typename T, bool K>
+__global__ void __launch_bounds__(640) k_nu_source(T* __restrict__ u, T* __restrict__ c, NuSrc q, int64_t px) {
+  const int i = threadIdx.x;
+  if (i >= 625) return;
+  const int oz = i / 25, ox = i - 25 * oz;
+  const double gz = q.gz[oz], gx = q.gx[ox];
+  if (gz == 0.0 || gx == 0.0) return;  // off the grid
+  const int64_t gi = (int64_t)(q.zs + oz - 12) * px + (q.xs + ox - 12);
+  const T delta = (T)(q.amp * gz * gx);
+  if constexpr (K) {
+    float v = u[gi], cc = c[gi];
+    kahan_add(v, cc, delta);
+    u[gi] = v;
+    c[gi] = cc;
+  } else {
+    u[gi] += delta;
+  }
+}
+
+// The source of step n on knots (slots 0 = z, 2 = x), as above.
+static NuSrc nu_source(const Shot& s, int64_t n) {
+  NuSrc q{};
+  q.zs = (int)s.src_idx[0];
+  q.xs = (int)s.src_idx[2];
+  double sum[2] = {0.0, 0.0};
+  for (int a = 0; a < 2; ++a) {
+    const int k = a == 0 ? 0 : 2;
+    const int N = (int)s.n[k];
+    auto coord = [&](int i) { return s.coords[k].empty() ? s.h[k] * i : s.coords[k][i]; };
+    const int i0 = (int)s.src_idx[k];
+    const double w = 2.0 * s.h[k];
+    double* g = a == 0 ? q.gz : q.gx;
+    for (int o = -12; o <= 12; ++o) {
+      const int i = i0 + o;
+      g[o + 12] = 0.0;
+      if (i < 0 || i > N) continue;
+      const double d = coord(i) - coord(i0);
+      g[o + 12] = std::exp(-d * d / (2.0 * w * w));
+      const double v = 0.5 * (coord(std::min(i + 1, N)) - coord(std::max(i - 1, 0)));  // dual cell width
+      sum[a] += g[o + 12] * v;
+    }
+  }
+  const double t = (double)n * s.d.dt + 0.5 * s.d.dt;
+  const double ar = M_PI * s.src_f0 * (t - s.src_t0);
+  const double rk = (1.0 - 2.0 * ar * ar) * std::exp(-ar * ar);
+  q.amp = s.d.dt * rk * s.src_amp / (sum[0] * sum[1]);
+  return q;
+}
+
 loss_status_t nu_ensure_axes(loss_ctx* h, Shot& s) {
   for (int k = 0; k < 3; ++k) {
     if (s.dim == 2 && k == 1) continue;
@@ -408,13 +465,20 @@ static loss_status_t nu_step_t(loss_ctx* h, Shot& s) {
   } else {
     NU_TRY((nu_update<T, K>(h, s, LOSS_FIELD_SIGMA, t0, t1, s.model[0], 0.0, -dt)));
   }
+  if (s.src_on && (s.src_kinds & LOSS_SRC_PRESSURE)) {
+    LaunchScope ls(h, LOSS_KERNEL_ACOUSTIC_X2);
+    k_nu_source<T, K><<<1, 640, 0, h->stream>>>((T*)s.field[LOSS_FIELD_SIGMA],
+                                                 K ? (T*)s.comp[LOSS_FIELD_SIGMA] : nullptr, nu_source(s, s.step), s.px);
+    NU_TRY(cuda_check(h, cudaGetLastError(), "non-uniform source kernel"));
+  }
   return half_A();
 }
 
 loss_status_t nu_step(loss_ctx* h, Shot& s) {
   if (s.d.physics != LOSS_ACOUSTIC || s.dim != 2)
     return fail_msg(h, LOSS_E_UNSUPPORTED, "time steps on non-uniform grids are built for 2-D acoustic grids");
-  if (s.src_on) return fail_msg(h, LOSS_E_UNSUPPORTED, "non-uniform grids: no point source");
+  if (s.src_on && (s.src_kinds & ~(uint32_t)LOSS_SRC_PRESSURE))
+    return fail_msg(h, LOSS_E_UNSUPPORTED, "non-uniform grids: pressure sources only");
   NU_TRY(nu_ensure_axes(h, s));
   if (s.esize == 8) return nu_step_t<double, false>(h, s);
   if (s.kahan) return nu_step_t<float, true>(h, s);
