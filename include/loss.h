@@ -322,10 +322,11 @@ loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis
 
 /* Non-uniform grid spacing along one axis (paper Sec. 3: the construction carries over to non-uniform grids; the
  * conclusion names it as future work).  x: HOST array of n[axis] + 1 finite, strictly increasing knot coordinates,
- * copied; NULL returns the axis to the uniform spacing h[axis].  On such an axis loss_derivative (first derivative)
- * and loss_pmbc_phi use the cubic spline on these knots: the PMBC weights are the junction rows of the global
- * natural spline's slope operator, truncated to |m| <= n_nb (FP64, built on the host), and each patch solves its
- * own slope system with the junction values as ends.  Layout and precision of the fields are unchanged.
+ * copied; NULL returns the axis to the uniform spacing h[axis].  On such an axis loss_derivative (first and second
+ * derivatives) and loss_pmbc_phi use the cubic spline on these knots: the PMBC weights are the junction rows of the
+ * global natural spline's slope operator, truncated to |m| <= n_nb (FP64, built on the host), and each patch solves
+ * its own slope system with the junction values as ends; the second derivative is the patch spline's, averaged
+ * over the two patches at a junction.  Layout and precision of the fields are unchanged.
  * loss_step on such a shot (2-D acoustic) takes the literal Strang step of Sec. 3.3 with every derivative on the
  * knots (other axes of the shot get equally spaced knots); the state stays at the integer time level.  An
  * absorbing layer (loss_set_pml, before or after this call) takes its profiles on the physical distance into the
@@ -333,8 +334,8 @@ loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis
  * its distance past the first physical knot over L.  A pressure source takes its Gaussian amplitude (width 2 h) on
  * the physical distance from the source knot over the same 25 knots per axis, normalised with the knots' dual cell
  * volumes so that it injects the uniform grid's total.  Returns LOSS_E_ARG for a bad axis or knots; afterwards
- * loss_gradient and loss_derivative_adjoint on the shot, loss_step on other shot kinds, and second derivatives on
- * the axis return LOSS_E_UNSUPPORTED. */
+ * loss_gradient and loss_derivative_adjoint on the shot and loss_step on other shot kinds return
+ * LOSS_E_UNSUPPORTED. */
 loss_status_t loss_set_coordinates(loss_handle_t handle, int32_t shot, int32_t axis, const double* x);
 
 /* Poll limit of the bounded waits of the staged FP32 x kernels (each block waits on an mbarrier for the bulk copies

@@ -1338,8 +1338,8 @@ static Tables tables_for(loss_ctx* h, const Shot& s, int k) {
 template <typename T>
 static loss_status_t run_derivative_t(loss_ctx* h, Shot& s, int k, const T* f, T* d1, T* d2, double* phi) {
   if (s.nu_tab[k]) {
-    if (d2) return fail(h, LOSS_E_UNSUPPORTED, "second derivatives on non-uniform axes are not built");
-    return run_nu_derivative<T>(h, s, k, f, d1, phi);
+    if (d2 && !d1) return fail(h, LOSS_E_ARG, "second derivatives on knots need the first derivative's array");
+    return run_nu_derivative<T>(h, s, k, f, d1, phi, d2);
   }
   const int64_t sy = s.len[2], sz = s.len[2] * s.len[1];
   LineGeom g;

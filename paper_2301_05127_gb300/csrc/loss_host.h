@@ -187,7 +187,7 @@ loss_status_t ensure_trace_capacity(loss_ctx* h, Shot& s, int64_t rows);
 loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d1, void* d2, double* phi, int mem);
 // loss_nonuniform.cu
 template <typename T>
-loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi);
+loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, T* d2 = nullptr);
 loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x);
 loss_status_t nu_step(loss_ctx* h, Shot& s);  // one Strang step of a shot with non-uniform axes (2-D acoustic)
 inline bool any_nonuniform(const Shot& s) { return s.nu_tab[0] || s.nu_tab[1] || s.nu_tab[2]; }

@@ -132,7 +132,7 @@ struct NuArgs {
   T* d1;
   double* phi;       // [lines][p + 1] or null
   const double* W;   // [(p + 1)][2 n_nb + 1]
-  const T* tab;      // A, G, L, IU, ra, rb: 6 x (n + 1)
+  const T* tab;      // A, G, L, IU, ra, rb, H (knot spacings h_i = x_{i+1} - x_i): 7 x (n + 1)
   int64_t lines, stride;
   int64_t outer_stride;  // base of line q: (q / inner) * outer_stride + (q % inner) * inner_mul
   int64_t inner, inner_mul;
@@ -194,6 +194,37 @@ __global__ void __launch_bounds__(128) k_nu_deriv(NuArgs<T> a) {
   if (l == a.p - 1) d[c1 * s] = (T)phR;
 }
 
+// Second derivative of the patched spline from the samples f and the slopes d1 (k_nu_deriv's output): on each
+// interval the spline is the cubic with values f_i, f_{i+1} and slopes d_i, d_{i+1}, whose second derivative is
+// 6 (f_{i+1} - f_i) / h^2 - (4 d_i + 2 d_{i+1}) / h at x_i and -6 (f_{i+1} - f_i) / h^2 + (2 d_i + 4 d_{i+1}) / h at
+// x_{i+1}.  Inside a patch the slope equations make the spline C^2, so one side serves; at a junction the two
+// patches' values are averaged, as for the uniform grid.  One thread per (line, patch), as k_nu_deriv.
+template <typename T>
+__global__ void __launch_bounds__(128) k_nu_d2(NuArgs<T> a, T* __restrict__ d2) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.lines * a.p) return;
+  const int l = (int)(tid / a.lines);
+  const int64_t q = tid - (int64_t)l * a.lines;
+  const int64_t base = (q / a.inner) * a.outer_stride + (q % a.inner) * a.inner_mul;
+  const T* f = a.f + base;
+  const T* d = a.d1 + base;
+  T* o = d2 + base;
+  const int64_t s = a.stride;
+  const T* H = a.tab + 6 * (int64_t)(a.n + 1);
+  auto right = [&](int i) {  // s''(x_i) on [x_i, x_{i+1}]
+    const T h = H[i];
+    return T(6) * (f[(i + 1) * s] - f[i * s]) / (h * h) - (T(4) * d[i * s] + T(2) * d[(i + 1) * s]) / h;
+  };
+  auto left = [&](int i) {  // s''(x_i) on [x_{i-1}, x_i]
+    const T h = H[i - 1];
+    return T(-6) * (f[i * s] - f[(i - 1) * s]) / (h * h) + (T(2) * d[(i - 1) * s] + T(4) * d[i * s]) / h;
+  };
+  const int c0 = l * a.M, c1 = c0 + a.M;
+  for (int i = c0 + 1; i < c1; ++i) o[i * s] = right(i);
+  o[c0 * s] = l == 0 ? right(c0) : T(0.5) * (left(c0) + right(c0));
+  if (l == a.p - 1) o[c1 * s] = left(c1);
+}
+
 // Uploads the tables of axis slot k of shot s (built from the knots x, n[k] + 1 of them).
 static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<double>& x) {
   NuHost t;
@@ -201,11 +232,13 @@ static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<do
   if (!nu_tables(x, s.p[k], s.d.n_nb, &t, &why)) return fail_msg(h, LOSS_E_ARG, why);
   const size_t np = (size_t)s.n[k] + 1;
   const size_t wbytes = t.W.size() * sizeof(double);
-  const size_t tbytes = 6 * np * s.esize;
+  const size_t tbytes = 7 * np * s.esize;
   std::vector<unsigned char> blob(wbytes + tbytes);
   std::memcpy(blob.data(), t.W.data(), wbytes);
-  const std::vector<double>* cols[6] = {&t.A, &t.G, &t.L, &t.IU, &t.ra, &t.rb};
-  for (int c = 0; c < 6; ++c)
+  std::vector<double> hs(np, 0.0);
+  for (size_t i = 0; i + 1 < np; ++i) hs[i] = x[i + 1] - x[i];
+  const std::vector<double>* cols[7] = {&t.A, &t.G, &t.L, &t.IU, &t.ra, &t.rb, &hs};
+  for (int c = 0; c < 7; ++c)
     for (size_t i = 0; i < np; ++i) {
       unsigned char* dst = blob.data() + wbytes + (c * np + i) * s.esize;
       if (s.esize == 8) {
@@ -228,7 +261,7 @@ static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<do
 // rows) and plane pitch pz: dense arrays have py = nx, pz = nx * ny; the handle's fields have py = s.sy, pz = s.sz.
 template <typename T>
 static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, int64_t py, int64_t pz,
-                               int kernel) {
+                               int kernel, T* d2 = nullptr) {
   NuArgs<T> a{};
   a.f = f;
   a.d1 = d1;
@@ -252,12 +285,16 @@ static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, d
   const int64_t threads = a.lines * a.p;
   LaunchScope ls(h, kernel);
   k_nu_deriv<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
+  if (d2 && d1) {
+    NU_TRY(cuda_check(h, cudaGetLastError(), "non-uniform derivative kernel"));
+    k_nu_d2<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a, d2);
+  }
   return cuda_check(h, cudaGetLastError(), "non-uniform derivative kernel");
 }
 
 template <typename T>
-loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi) {
-  return nu_launch<T>(h, s, k, f, d1, phi, s.len[2], s.len[2] * s.len[1], LOSS_KERNEL_DERIVATIVE);
+loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, T* d2) {
+  return nu_launch<T>(h, s, k, f, d1, phi, s.len[2], s.len[2] * s.len[1], LOSS_KERNEL_DERIVATIVE, d2);
 }
 
 // --- time step on grids with non-uniform axes (2-D acoustic) ------------------------------------------------
@@ -485,8 +522,8 @@ loss_status_t nu_step(loss_ctx* h, Shot& s) {
   return nu_step_t<float, false>(h, s);
 }
 
-template loss_status_t run_nu_derivative<float>(loss_ctx*, Shot&, int, const float*, float*, double*);
-template loss_status_t run_nu_derivative<double>(loss_ctx*, Shot&, int, const double*, double*, double*);
+template loss_status_t run_nu_derivative<float>(loss_ctx*, Shot&, int, const float*, float*, double*, float*);
+template loss_status_t run_nu_derivative<double>(loss_ctx*, Shot&, int, const double*, double*, double*, double*);
 
 loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x) {
   if (!x) {

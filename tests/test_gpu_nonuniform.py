@@ -1,6 +1,7 @@
 """GPU parity of the LOSS derivative on non-uniform grids (loss_set_coordinates; the paper's Sec. 3 remark and its
 conclusion) against the oracle's B-spline collocation on the same knots (oracle/nonuniform.py), element by
-element: first derivatives and PMBC junction values, 2-D and 3-D, FP64 and FP32, several axes and patch counts."""
+element: first and second derivatives and PMBC junction values, 2-D and 3-D, FP64 and FP32, several axes and
+patch counts; and the 2-D acoustic step on such grids, with absorbing layers and pressure sources."""
 import numpy as np
 import pytest
 
@@ -54,6 +55,11 @@ def test_nonuniform_derivative_and_phi_match_oracle(pkg, case, prec):
         got = g.derivative(0, a, f).astype(np.float64)
         assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max(), (a, prec)
         if a in knots:
+            _, ref2 = nu.derivative(f.astype(np.float64), a, x, p[a], n_nb, second=True)
+            got1, got2 = g.derivative(0, a, f, second=True)
+            assert np.array_equal(got1, g.derivative(0, a, f)), (a, prec)
+            tol2 = 1e-10 if prec == "fp64" else 5e-4
+            assert np.abs(got2.astype(np.float64) - ref2).max() <= tol2 * np.abs(ref2).max(), (a, prec)
             fm = np.moveaxis(f.astype(np.float64), a, -1).reshape(-1, n[a] + 1)
             ref_phi = nu.pmbc_phi(fm, x, p[a], n_nb)
             got_phi = g.pmbc_phi(0, a, f)
@@ -89,7 +95,7 @@ def test_nonuniform_rejections(pkg):
     g.set_coordinates(0, 0, _knots(32, 1))
     f = np.zeros(g.shape())
     with pytest.raises(pkg.LossError) as e:
-        g.derivative(0, 0, f, second=True)
+        g.derivative_adjoint(0, 0, f)
     assert e.value.status == pkg.LOSS_E_UNSUPPORTED
     g.set_model(0, np.full(g.shape(), 2000.0), None, np.full(g.shape(), 1000.0))
     g.set_source(0, [16, 0, 16], pkg.LOSS_SRC_PRESSURE, 1.0, 20.0, 0.06)
