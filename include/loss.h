@@ -333,9 +333,9 @@ loss_status_t loss_derivative_noalloc(const loss_grid_desc_t* desc, int32_t axis
  * layer: on each side L = the layer's physical width and d0 = -3 vmax ln R / (2 L), the normalised depth of a knot
  * its distance past the first physical knot over L.  A pressure source takes its Gaussian amplitude (width 2 h) on
  * the physical distance from the source knot over the same 25 knots per axis, normalised with the knots' dual cell
- * volumes so that it injects the uniform grid's total.  Returns LOSS_E_ARG for a bad axis or knots; afterwards
- * loss_gradient and loss_derivative_adjoint on the shot and loss_step on other shot kinds return
- * LOSS_E_UNSUPPORTED. */
+ * volumes so that it injects the uniform grid's total.  loss_derivative_adjoint on the axis applies the exact
+ * transpose of this derivative.  Returns LOSS_E_ARG for a bad axis or knots; afterwards loss_gradient on the shot
+ * and loss_step on other shot kinds return LOSS_E_UNSUPPORTED. */
 loss_status_t loss_set_coordinates(loss_handle_t handle, int32_t shot, int32_t axis, const double* x);
 
 /* Poll limit of the bounded waits of the staged FP32 x kernels (each block waits on an mbarrier for the bulk copies

@@ -437,6 +437,7 @@ loss_status_t run_gradient(loss_ctx* h, Shot& s, const double* d_obs, int32_t ch
 // Stand-alone D^T along internal slot k of dense arrays (DEVICE pointers).
 template <typename T>
 static loss_status_t derivative_adjoint_t(loss_ctx* h, Shot& s, int k, const T* g, T* out) {
+  if (s.nu_tab[k]) return run_nu_derivative_adjoint<T>(h, s, k, g, out);  // an axis with knots
   const int64_t sy = s.len[2], sz = s.len[2] * s.len[1];
   LineGeom geo;
   int logc, threads;

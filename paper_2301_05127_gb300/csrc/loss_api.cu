@@ -1168,7 +1168,6 @@ loss_status_t loss_derivative_adjoint(loss_handle_t h, int32_t shot, int32_t axi
                                       int32_t mem) {
   Shot* s;
   LOSS_TRY(get_shot(h, shot, &s));
-  if (any_nonuniform(*s)) return fail(h, LOSS_E_UNSUPPORTED, "adjoints on non-uniform grids are not built");
   if (axis < 0 || axis >= s->dim) return fail(h, LOSS_E_ARG, "axis out of range");
   if (!g || !out || (mem != LOSS_MEM_HOST && mem != LOSS_MEM_DEVICE)) return fail(h, LOSS_E_ARG, "bad buffers");
   return run_derivative_adjoint(h, *s, axis_slot(*s, axis), g, out, mem);

@@ -188,6 +188,8 @@ loss_status_t run_derivative(loss_ctx* h, Shot& s, int k, const void* f, void* d
 // loss_nonuniform.cu
 template <typename T>
 loss_status_t run_nu_derivative(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, T* d2 = nullptr);
+template <typename T>
+loss_status_t run_nu_derivative_adjoint(loss_ctx* h, Shot& s, int k, const T* g, T* out);
 loss_status_t set_coordinates(loss_ctx* h, Shot& s, int k, const double* x);
 loss_status_t nu_step(loss_ctx* h, Shot& s);  // one Strang step of a shot with non-uniform axes (2-D acoustic)
 inline bool any_nonuniform(const Shot& s) { return s.nu_tab[0] || s.nu_tab[1] || s.nu_tab[2]; }

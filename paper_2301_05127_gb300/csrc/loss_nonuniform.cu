@@ -225,6 +225,91 @@ __global__ void __launch_bounds__(128) k_nu_d2(NuArgs<T> a, T* __restrict__ d2) 
   if (l == a.p - 1) o[c1 * s] = left(c1);
 }
 
+// Transpose of the derivative on knots, out = D^T g, in two passes.  The forward operator per (line, patch) is
+// d_int = T^{-1} r with r_i = -RA_i f_{i-1} + (RA_i - RB_i) f_i + RB_i f_{i+1} - A_{c0+1} phi_L [i = c0 + 1]
+// - G_{c1-1} phi_R [i = c1 - 1], d at the patch's first knot = phi_L (and at the line's last knot = phi_R), and
+// phi_j = sum_m W[j][m] f_{jM+m}.  Pass 1, per (line, patch): y = T^{-T} g_int by the transposed Thomas factors
+// (T = L U: U^T z = g forward, L^T y = z backward), the interior f-bar = R^T y at the patch's interior knots, and
+// into scratch the patch's contributions at its two end knots (from R^T) and to its two junction sums (from the
+// phi terms and the junction outputs).  Pass 2, per sample: the end-knot contributions of both patches at a
+// junction and W^T applied to the junction adjoints, in FP64 as the forward junction sums.
+template <typename T>
+__global__ void __launch_bounds__(128) k_nu_adj1(NuArgs<T> a, const T* __restrict__ gin, T* __restrict__ out,
+                                                 double* __restrict__ scr) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = a.lines * a.p;
+  if (tid >= nt) return;
+  const int l = (int)(tid / a.lines);
+  const int64_t q = tid - (int64_t)l * a.lines;
+  const int64_t base = (q / a.inner) * a.outer_stride + (q % a.inner) * a.inner_mul;
+  const T* g = gin + base;
+  T* o = out + base;
+  const int64_t s = a.stride;
+  const int np = a.n + 1;
+  const T* A = a.tab;
+  const T* G = A + np;
+  const T* L = G + np;
+  const T* IU = L + np;
+  const T* RA = IU + np;
+  const T* RB = RA + np;
+  const int c0 = l * a.M, c1 = c0 + a.M;
+  T zp = T(0);
+  for (int i = c0 + 1; i < c1; ++i) {  // U^T z = g
+    const T z = (g[i * s] - (i > c0 + 1 ? G[i - 1] * zp : T(0))) * IU[i];
+    o[i * s] = z;
+    zp = z;
+  }
+  T yn = T(0);
+  for (int i = c1 - 1; i > c0; --i) {  // L^T y = z
+    const T y = o[i * s] - (i < c1 - 1 ? L[i + 1] * yn : T(0));
+    o[i * s] = y;
+    yn = y;
+  }
+  const T y0 = o[(c0 + 1) * s], y1 = o[(c1 - 1) * s];
+  T yprev = T(0);
+  for (int i = c0 + 1; i < c1; ++i) {  // f-bar = R^T y at the interior knots
+    const T yi = o[i * s];
+    T fb = (RA[i] - RB[i]) * yi;
+    if (i + 1 < c1) fb -= RA[i + 1] * o[(i + 1) * s];
+    if (i - 1 > c0) fb += RB[i - 1] * yprev;
+    o[i * s] = fb;
+    yprev = yi;
+  }
+  scr[tid] = -(double)RA[c0 + 1] * (double)y0;                       // f-bar at the first knot
+  scr[nt + tid] = (double)RB[c1 - 1] * (double)y1;                   // f-bar at the last knot
+  scr[2 * nt + tid] = (double)g[c0 * s] - (double)A[c0 + 1] * (double)y0;  // adjoint of phi_L
+  scr[3 * nt + tid] = -(double)G[c1 - 1] * (double)y1 + (l == a.p - 1 ? (double)g[c1 * s] : 0.0);  // of phi_R
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_nu_adj2(NuArgs<T> a, T* __restrict__ out, const double* __restrict__ scr) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int np = a.n + 1;
+  if (tid >= a.lines * np) return;
+  const int64_t q = tid / np;
+  const int i = (int)(tid - q * np);
+  const int64_t nt = a.lines * a.p;
+  const int64_t base = (q / a.inner) * a.outer_stride + (q % a.inner) * a.inner_mul;
+  T* o = out + base + (int64_t)i * a.stride;
+  auto at = [&](int part, int l) { return scr[part * nt + (int64_t)l * a.lines + q]; };
+  double acc = 0.0;
+  const bool junction = i % a.M == 0;
+  if (junction) {
+    const int j = i / a.M;
+    if (j >= 1) acc += at(1, j - 1);
+    if (j < a.p) acc += at(0, j);
+  }
+  const int wl = 2 * a.n_nb + 1;
+  const int jlo = max(0, (i - a.n_nb + a.M - 1) / a.M), jhi = min(a.p, (i + a.n_nb) / a.M);
+  for (int j = jlo; j <= jhi; ++j) {
+    const int m = i - j * a.M;
+    if (m < -a.n_nb || m > a.n_nb) continue;
+    const double pb = (j >= 1 ? at(3, j - 1) : 0.0) + (j < a.p ? at(2, j) : 0.0);
+    acc = fma(a.W[(size_t)j * wl + (m + a.n_nb)], pb, acc);
+  }
+  *o = junction ? (T)acc : (T)((double)*o + acc);
+}
+
 // Uploads the tables of axis slot k of shot s (built from the knots x, n[k] + 1 of them).
 static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<double>& x) {
   NuHost t;
@@ -260,12 +345,8 @@ static loss_status_t nu_upload(loss_ctx* h, Shot& s, int k, const std::vector<do
 // Derivative along axis slot k of a field stored with row pitch py (elements between consecutive y, or z in 2-D,
 // rows) and plane pitch pz: dense arrays have py = nx, pz = nx * ny; the handle's fields have py = s.sy, pz = s.sz.
 template <typename T>
-static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, int64_t py, int64_t pz,
-                               int kernel, T* d2 = nullptr) {
-  NuArgs<T> a{};
-  a.f = f;
-  a.d1 = d1;
-  a.phi = phi;
+static void nu_args(const Shot& s, int k, int64_t py, int64_t pz, NuArgs<T>* pa) {
+  NuArgs<T>& a = *pa;
   a.W = (const double*)s.nu_tab[k];
   const size_t wl = 2 * (size_t)s.d.n_nb + 1;
   a.tab = (const T*)((const unsigned char*)s.nu_tab[k] + (s.p[k] + 1) * wl * sizeof(double));
@@ -282,6 +363,16 @@ static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, d
   } else {  // z lines: q = y * nx + x
     a.stride = pz, a.inner = nx, a.inner_mul = 1, a.outer_stride = py;
   }
+}
+
+template <typename T>
+static loss_status_t nu_launch(loss_ctx* h, Shot& s, int k, const T* f, T* d1, double* phi, int64_t py, int64_t pz,
+                               int kernel, T* d2 = nullptr) {
+  NuArgs<T> a{};
+  nu_args(s, k, py, pz, &a);
+  a.f = f;
+  a.d1 = d1;
+  a.phi = phi;
   const int64_t threads = a.lines * a.p;
   LaunchScope ls(h, kernel);
   k_nu_deriv<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
@@ -521,6 +612,27 @@ loss_status_t nu_step(loss_ctx* h, Shot& s) {
   if (s.kahan) return nu_step_t<float, true>(h, s);
   return nu_step_t<float, false>(h, s);
 }
+
+template <typename T>
+loss_status_t run_nu_derivative_adjoint(loss_ctx* h, Shot& s, int k, const T* g, T* out) {
+  NuArgs<T> a{};
+  nu_args(s, k, s.len[2], s.len[2] * s.len[1], &a);
+  const int64_t nt = a.lines * a.p;
+  void* scr = nullptr;
+  NU_TRY(dev_alloc(h, (size_t)4 * nt * sizeof(double), &scr));
+  LaunchScope ls(h, LOSS_KERNEL_ADJOINT);
+  k_nu_adj1<T><<<(unsigned)((nt + 127) / 128), 128, 0, h->stream>>>(a, g, out, (double*)scr);
+  loss_status_t st = cuda_check(h, cudaGetLastError(), "non-uniform adjoint kernel");
+  if (st == LOSS_OK) {
+    const int64_t ne = a.lines * (a.n + 1);
+    k_nu_adj2<T><<<(unsigned)((ne + 255) / 256), 256, 0, h->stream>>>(a, out, (const double*)scr);
+    st = cuda_check(h, cudaGetLastError(), "non-uniform adjoint kernel");
+  }
+  dev_free(h, scr);
+  return st;
+}
+template loss_status_t run_nu_derivative_adjoint<float>(loss_ctx*, Shot&, int, const float*, float*);
+template loss_status_t run_nu_derivative_adjoint<double>(loss_ctx*, Shot&, int, const double*, double*);
 
 template loss_status_t run_nu_derivative<float>(loss_ctx*, Shot&, int, const float*, float*, double*, float*);
 template loss_status_t run_nu_derivative<double>(loss_ctx*, Shot&, int, const double*, double*, double*, double*);

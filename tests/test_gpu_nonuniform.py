@@ -1,7 +1,7 @@
 """GPU parity of the LOSS derivative on non-uniform grids (loss_set_coordinates; the paper's Sec. 3 remark and its
 conclusion) against the oracle's B-spline collocation on the same knots (oracle/nonuniform.py), element by
-element: first and second derivatives and PMBC junction values, 2-D and 3-D, FP64 and FP32, several axes and
-patch counts; and the 2-D acoustic step on such grids, with absorbing layers and pressure sources."""
+element: first and second derivatives, their transpose and PMBC junction values, 2-D and 3-D, FP64 and FP32, several
+axes and patch counts; and the 2-D acoustic step on such grids, with absorbing layers and pressure sources."""
 import numpy as np
 import pytest
 
@@ -67,6 +67,26 @@ def test_nonuniform_derivative_and_phi_match_oracle(pkg, case, prec):
     g.close()
 
 
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonuniform_derivative_adjoint_matches_the_oracles_transpose(pkg, case, prec):
+    """loss_derivative_adjoint on axes with knots against the transpose of the oracle's derivative operator, built
+    column by column from unit vectors: D^T g along every line, element by element."""
+    dim, n, p, n_nb, axes = case
+    d = pkg.make_desc(dim, pkg.LOSS_ACOUSTIC, pkg.PRECISIONS[prec], n_nb, n, p, (10.0,) * dim, 1e-3)
+    g = pkg.Grid([d])
+    knots = {a: _knots(n[a], 200 + a) for a in axes}
+    for a, x in knots.items():
+        g.set_coordinates(0, a, x)
+    G = np.random.default_rng(9).standard_normal(g.shape()).astype(g.dtype)
+    for a, x in knots.items():
+        D = nu.derivative_1d(np.eye(n[a] + 1), x, p[a], n_nb).T  # D[:, c] = D e_c
+        ref = np.moveaxis(np.moveaxis(G.astype(np.float64), a, -1) @ D, -1, a)
+        got = g.derivative_adjoint(0, a, G).astype(np.float64)
+        assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max(), (a, prec)
+    g.close()
+
+
 def test_uniform_knots_equal_the_uniform_path(pkg):
     """Knots with equal spacing through the non-uniform kernel give the uniform LOSS derivative (to rounding)."""
     n, p, n_nb, h = (40, 56), (2, 4), 10, (2.5, 4.0)
@@ -93,9 +113,8 @@ def test_nonuniform_rejections(pkg):
         g.set_coordinates(0, 0, bad)
     assert e.value.status == pkg.LOSS_E_ARG
     g.set_coordinates(0, 0, _knots(32, 1))
-    f = np.zeros(g.shape())
-    with pytest.raises(pkg.LossError) as e:
-        g.derivative_adjoint(0, 0, f)
+    with pytest.raises(pkg.LossError) as e:  # gradients through the step on knots are not built
+        g.gradient(0, np.zeros((1, 1)), 1)
     assert e.value.status == pkg.LOSS_E_UNSUPPORTED
     g.set_model(0, np.full(g.shape(), 2000.0), None, np.full(g.shape(), 1000.0))
     g.set_source(0, [16, 0, 16], pkg.LOSS_SRC_PRESSURE, 1.0, 20.0, 0.06)
