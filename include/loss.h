@@ -189,6 +189,8 @@ loss_status_t loss_pmbc_phi(loss_handle_t handle, int32_t shot, int32_t axis, co
  * arrays, layouts and memory rules; out is overwritten).  Per line D = (3/h) P with P f = e the compact solve
  * of every patch closed by the PMBC junction values (Sec. 3.2); P^T runs the same symmetric tridiagonal solve
  * on the patch interiors (zero junction values) and scatters the junction adjoints back with the PMBC weights.
+ * On an axis with knots (loss_set_coordinates) it is the transpose of that axis's spline derivative: the patch
+ * slope systems are not symmetric there, so their transposed factors are used.
  * The paper has no counterpart: it is the building block of loss_gradient.  Errors as loss_derivative. */
 loss_status_t loss_derivative_adjoint(loss_handle_t handle, int32_t shot, int32_t axis, const void* g, void* out,
                                       int32_t mem);
